@@ -1,0 +1,132 @@
+"""Inexact Gauss-Newton-Krylov solver of the oracle (Sec. 3.2, Eq. 11): spectral
+(DCT) preconditioner, preconditioned CG, Armijo backtracking.  FP64, numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Readings of the paper taken here:
+* The preconditioner is the regularizer's Hessian plus gamma, P = alpha dt h^d A +
+  gamma I, applied through its DCT-II eigen-decomposition; a zero eigenvalue
+  (gamma = 0, constant mode) is replaced by 1, i.e. the pseudo-inverse plus
+  the identity on the null space.  For the elastic model only its mu-Laplacian
+  part is used.
+* Stopping and line-search constants are the textbook ones (the paper defers
+  to FAIR's defaults): PCG stops at relative residual 0.1 or 50 iterations
+  (Sec. 4.1); Armijo starts at mu = 1, halves, c = 1e-4, at most 10 trials;
+  Gauss-Newton stops when |g| <= gtol |g0|.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.fft import dctn, idctn
+
+from .objective import Problem, gradient, hessvec, objective
+
+
+def laplacian_eigenvalues(prob: Problem) -> np.ndarray:
+    """Eigenvalues of the Neumann Laplacian A on the velocity grid, arranged like
+    the DCT-II coefficients of one (z, y, x) block."""
+    g = prob.vgrid
+    lam = np.zeros(g.shape)
+    for a in range(g.d):
+        k = np.arange(g.m[a])
+        e = (2.0 - 2.0 * np.cos(np.pi * k / g.m[a])) / g.h[a] ** 2
+        shape = [1] * g.d
+        shape[g.d - 1 - a] = g.m[a]
+        lam = lam + e.reshape(shape)
+    return lam
+
+
+def preconditioner_eigenvalues(prob: Problem) -> np.ndarray:
+    """Diagonal of P = alpha dt h^d A_reg + gamma I in the DCT-II basis, with zeros
+    replaced by 1."""
+    lam = laplacian_eigenvalues(prob)
+    if prob.reg == "curvature":
+        lam = lam * lam
+    elif prob.reg == "elastic":
+        lam = prob.mu * lam
+    p = prob.alpha * prob.time_weight * prob.vgrid.cell_volume * lam + prob.gamma
+    return np.where(p == 0.0, 1.0, p)
+
+
+def apply_preconditioner(prob: Problem, r: np.ndarray) -> np.ndarray:
+    """P^+ r, block by block over time nodes and components (DCT-II, divide, DCT-III)."""
+    ev = preconditioner_eigenvalues(prob)
+    out = np.zeros_like(r, dtype=np.float64)
+    for j in range(r.shape[0]):
+        for c in range(r.shape[1]):
+            out[j, c] = idctn(dctn(r[j, c], type=2, norm="ortho") / ev, type=2, norm="ortho")
+    return out
+
+
+def pcg(Hfun, b, Minv=None, tol=0.1, maxit=50):
+    """Preconditioned conjugate gradients for H x = b from x0 = 0 (Hestenes-Stiefel).
+    Stops when |r| <= tol |b| or after maxit iterations, or on non-positive
+    curvature p^T H p <= 0.  Returns (x, iterations, relative residual)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    nb = np.sqrt(np.sum(b * b))
+    if nb == 0.0:
+        return x, 0, 0.0
+    z = Minv(r) if Minv is not None else r.copy()
+    p = z.copy()
+    rz = np.sum(r * z)
+    it = 0
+    for it in range(1, maxit + 1):
+        Hp = Hfun(p)
+        pHp = np.sum(p * Hp)
+        if pHp <= 0.0:
+            it -= 1
+            break
+        a = rz / pHp
+        x = x + a * p
+        r = r - a * Hp
+        if np.sqrt(np.sum(r * r)) <= tol * nb:
+            break
+        z = Minv(r) if Minv is not None else r.copy()
+        rz_new = np.sum(r * z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, float(np.sqrt(np.sum(r * r)) / nb)
+
+
+def armijo(Jfun, v, J0, g, dv, c=1e-4, max_trials=10):
+    """Backtracking line search: the first mu in 1, 1/2, 1/4, ... with
+    J(v + mu dv) <= J0 + c mu g^T dv.  Returns (mu, J(v + mu dv)) or (0, J0)."""
+    slope = float(np.sum(g * dv))
+    mu = 1.0
+    for _ in range(max_trials):
+        Jt = Jfun(v + mu * dv)
+        if Jt <= J0 + c * mu * slope:
+            return mu, Jt
+        mu *= 0.5
+    return 0.0, J0
+
+
+def gauss_newton(prob: Problem, T, R, v0, max_gn=10, gtol=1e-3, max_pcg=50,
+                 pcg_tol=0.1, precond=True, log=None):
+    """Inexact Gauss-Newton-Krylov with Armijo (Eq. 11).  Returns (v, report)."""
+    v = np.array(v0, dtype=np.float64, copy=True)
+    J, D, S, _ = objective(prob, v, T, R)
+    g = gradient(prob, v, T, R)
+    g0 = float(np.sqrt(np.sum(g * g)))
+    rep = {"J0": J, "g0": g0, "iters": 0, "pcg_iters": 0, "history": []}
+    Minv = (lambda r: apply_preconditioner(prob, r)) if precond else None
+    for it in range(max_gn):
+        gn = float(np.sqrt(np.sum(g * g)))
+        if gn <= gtol * g0:
+            break
+        dv, pit, rel = pcg(lambda p: hessvec(prob, v, T, p), -g, Minv, pcg_tol, max_pcg)
+        mu, Jt = armijo(lambda w: objective(prob, w, T, R)[0], v, J, g, dv)
+        rep["history"].append({"J": J, "g": gn, "pcg": pit, "relres": rel, "mu": mu})
+        rep["pcg_iters"] += pit
+        rep["iters"] = it + 1
+        if log:
+            log(rep["history"][-1])
+        if mu == 0.0:
+            rep["status"] = "line search failed"
+            break
+        v = v + mu * dv
+        J, D, S, _ = objective(prob, v, T, R)
+        g = gradient(prob, v, T, R)
+    rep.update({"J": J, "D": D, "S": S, "g": float(np.sqrt(np.sum(g * g)))})
+    return v, rep
