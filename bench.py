@@ -1,0 +1,354 @@
+"""Benchmark of the Lagrangian Gauss-Newton-Krylov hot path on GB300.
+
+One step = one Gauss-Newton Hessian matvec H dv (Sec. 3.2) on the 3D
+intensity-preserving workload: 128^3 template, stationary velocity on 64^3 x 3
+(786,432 unknowns), N = 8 RK4 steps, trilinear interpolation, diffusion
+regularizer.  The matvec runs through the library's public call (``hessvec``):
+velocity/template/direction packing, the fused J^T h^d J kernel, the gradient
+unpack and the regularizer stencil.  Inputs are seeded synthetic data shaped
+like the paper's 3D problems.
+
+Printed (one JSON line, rank 0):
+  value     Hessian matvecs/s over all ranks (inputs resident in HBM; L2 flushed
+            between timed matvecs by a 512 MiB write, flush not timed)
+  e2e       the same metric with the inputs copied from pinned host memory and
+            the result copied back inside every timed step
+  roofline  the fused matvec kernel: algorithmic bytes / its CUDA-event time,
+            against the measured HBM copy bandwidth
+  cpu_baseline  the FP64 oracle's matvec on a sample of voxels, host cores
+  extra     forward voxel-steps/s and the time-to-solution of one zero-start
+            Gauss-Newton solve to a 1e-3 gradient-norm drop (outside the timed
+            region)
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(bounded sample per step).  Multi-GPU runs (torchrun) are replicas: every rank
+solves its own seeded problem, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "3d_transport_128"
+METRIC = "Hessian matvecs/s (3D 128^3 transport, v 64^3x3 stationary, N=8 RK4, trilinear)"
+UNIT = "matvec/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- inputs --
+
+def make_problem(seed):
+    from paper_1703_04446_gb300 import synth
+    ins = synth.make_inputs(WORKLOAD, seed=seed)
+    wl = ins["workload"]
+    dv = synth.random_velocity(wl.velocity, wl.time_nodes, 0.5 * max(wl.image.h) * 8, seed + 11)
+    ins["dv"] = np.ascontiguousarray(dv, dtype=np.float32)
+    return ins
+
+
+def algorithmic_bytes_hess(wl):
+    """Compulsory HBM bytes of one fused J^T h^d J launch: read v and dv (n floats
+    each), read T (M floats), write the gradient accumulator (n floats)."""
+    n = wl.time_nodes * wl.image.d * int(np.prod(wl.velocity.m))
+    M = int(np.prod(wl.image.m))
+    return 4 * (3 * n + M)
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def oracle_hessvec_sample(ins, frac, seed=0):
+    """The oracle's matvec restricted to a random subset of the voxels (the
+    per-voxel terms J_i^T h^d J_i dv of Sec. 3.2 are independent), plus the
+    regularizer on the full grid.  Returns (fraction of a full matvec, seconds)."""
+    from oracle import lagrangian as L
+    from oracle.objective import Problem as OP, reg_operator
+    wl = ins["workload"]
+    ig = L.Grid(wl.image.m, wl.image.lo, wl.image.hi)
+    vg = L.Grid(wl.velocity.m, wl.velocity.lo, wl.velocity.hi)
+    op = OP(ig, vg, K=wl.time_nodes, N=wl.rk4_steps, model=wl.model, reg=wl.regularizer, alpha=wl.alpha,
+            gamma=wl.gamma)
+    v = ins["v0"].astype(np.float64)
+    dv = ins["dv"].astype(np.float64)
+    T = ins["T"].astype(np.float64)
+    xc = L.cell_centres(ig)
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(xc.shape[1], size=max(1, int(frac * xc.shape[1])), replace=False)
+    t0 = time.perf_counter()
+    y, dy, hist = L.characteristics(v, vg, xc[:, idx], wl.rk4_steps, -1, dv=dv, keep=True)
+    _, gT = L.interpolate(T, ig, y, gradient=True)
+    du = np.sum(gT * dy, axis=0)
+    g = L.characteristics_adjoint(v, vg, hist, wl.rk4_steps, -1, ig.cell_volume * du * gT)
+    g = g + op.alpha * reg_operator(op, dv) + op.gamma * dv
+    secs = time.perf_counter() - t0
+    return len(idx) / xc.shape[1], secs
+
+
+def cpu_baseline(ins, target_s=12.0):
+    frac = 1.0 / 512
+    f, s = oracle_hessvec_sample(ins, frac)
+    if s < target_s / 4:
+        frac = min(1.0, frac * target_s / max(s, 1e-3))
+        f, s = oracle_hessvec_sample(ins, frac, seed=1)
+    return {"value": f / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle matvec on {f * 100:.2f}% of the 128^3 voxels "
+                      f"({int(round(f * 128 ** 3))} characteristics, N=8) plus the full regularizer, "
+                      f"{s:.1f} s; value = sampled fraction of a matvec / time"}
+
+
+# ------------------------------------------------------------------- main --
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    ins = make_problem(seed=0)
+    frac = 1.0 / 1024
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_hessvec_sample(ins, frac / 4)
+    tot_f, tot_s = 0.0, 0.0
+    for k in range(args.steps):
+        f, s = oracle_hessvec_sample(ins, frac, seed=k)
+        tot_f += f
+        tot_s += s
+    val = tot_f / tot_s
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "image": [128, 128, 128], "velocity": [64, 64, 64, 3],
+                       "rk4_steps": 8, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{frac * 100:.3f}% of the voxels per step (per-voxel terms of the "
+                                       "Gauss-Newton matvec) plus the full regularizer"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1703_04446_gb300 import lgnk
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ins = make_problem(seed=rank)
+    wl = ins["workload"]
+    prob = lgnk.Problem.from_workload(wl)
+    ctx = lgnk.Context(prob, device=dev)
+    tv, tT, tR, tdv = (torch.from_numpy(ins[k]).to(dev) for k in ("v0", "T", "R", "dv"))
+    out = torch.empty_like(tv)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        ctx.hessvec(tv, tT, tdv, out)
+    barrier()
+
+    # timed region: K matvecs, each between CUDA events; L2 flushed between them
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            ctx.hessvec(tv, tT, tdv, out)
+            ends[k].record(stream)
+        barrier()
+    kern_ms, kern_n, launches = ctx.profile_read()
+    ctx.profile(False)
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = float(t.item())
+    value = world * 1000.0 / step_ms
+
+    # end to end through the public call: pinned host inputs in, result out
+    hv, hT, hdv = (torch.from_numpy(ins[k]).pin_memory() for k in ("v0", "T", "dv"))
+    hout = torch.empty(tv.shape, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        dv_, T_, ddv = hv.to(dev, non_blocking=True), hT.to(dev, non_blocking=True), hdv.to(dev, non_blocking=True)
+        hout.copy_(ctx.hessvec(dv_, T_, ddv), non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dv_, T_, ddv = hv.to(dev, non_blocking=True), hT.to(dev, non_blocking=True), hdv.to(dev, non_blocking=True)
+        hout.copy_(ctx.hessvec(dv_, T_, ddv), non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+
+    # extras outside the timed region: forward throughput, time-to-solution
+    fwd_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        ctx.forward(tv, tT)
+    fwd_ev[0].record(stream)
+    for _ in range(10):
+        ctx.forward(tv, tT)
+    fwd_ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = fwd_ev[0].elapsed_time(fwd_ev[1]) / 10
+    voxel_steps = int(np.prod(wl.image.m)) * wl.rk4_steps
+    tts = None
+    if not args.no_solve:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, rep = ctx.solve(tT, tR, None, max_gn=args.max_gn, gn_grad_rtol=1e-3, max_pcg=50, pcg_rtol=0.1)
+        torch.cuda.synchronize(dev)
+        tts = {"seconds": time.perf_counter() - t0, "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters"],
+               "hessvecs": rep["hessvecs"], "grad_ratio": rep["g"] / rep["g0"], "J0": rep["J0"], "J": rep["J"],
+               "status": rep["status_name"], "max_gn": args.max_gn}
+
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    kern_avg_ms = kern_ms / max(kern_n, 1)
+    alg = algorithmic_bytes_hess(wl)
+    achieved = alg / (kern_avg_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "hess_kernel_dram.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("traffic_bytes_per_launch")
+        except Exception:
+            traffic = None
+    n = int(tv.numel())
+    M = int(tT.numel())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": list(wl.image.m), "velocity": list(wl.velocity.m) + [3],
+                   "time_nodes": wl.time_nodes, "rk4_steps": wl.rk4_steps, "unknowns": n,
+                   "regularizer": wl.regularizer, "l2": "flushed between timed steps (512 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 4 * (2 * n + M),
+                "d2h_bytes_per_step": 4 * n},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "trace_kernel<3,stat,transport,HESS>",
+                     "kernel_ms": kern_avg_ms, "algorithmic_bytes": alg, "peak_kind": peak_kind},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "extra": {"forward_voxel_steps_per_s": voxel_steps / (fwd_ms * 1e-3), "forward_ms": fwd_ms,
+                  "time_to_solution": tts},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(ins)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lgnk", choices=["lgnk", "reference"])
+    ap.add_argument("--max-gn", type=int, default=30)
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * lgnk.h - C ABI of the GB300 Lagrangian Gauss-Newton-Krylov hot path.
+ *
+ * The method (Mang & Ruthotto, arXiv 1703.04446): a velocity v(x, t) moves the
+ * template T along characteristics (Eq. 4) computed by RK4 with N steps
+ * (Alg. 1).  The final state u1(v) is the transport pull-back
+ * u1 = T(y(v, x_c, 1, 0)) (Eq. 6, intensity preserving) or the particle-in-cell
+ * push-forward u1 = F(y(v, x_c, 0, 1)) T(x_c) (Eqs. 7-8, mass preserving).
+ * Registration minimises J(v) = D(u1(v), R) + alpha S(v) (Eq. 9) with the SSD
+ * distance (Eq. 10) by an inexact Gauss-Newton-Krylov method (Eq. 11).
+ *
+ * Conventions for every call below:
+ *  - Array arguments are DEVICE pointers owned by the caller, contiguous
+ *    float32, 16-byte aligned (what cudaMalloc and torch return), unless the
+ *    argument says "host".
+ *  - A grid with m = (m_x, m_y[, m_z]) cells on [lo, hi] has its points at the
+ *    cell centres lo + (i + 1/2) h (Sec. 3).  Images have M = prod(m) values,
+ *    x fastest: index = (z * m_y + y) * m_x + x.
+ *  - A velocity has n = K * d * M_v values in layout [K][d][z][y][x]:
+ *    K time nodes at t_j = j / (K - 1) (K = 1: stationary), d components
+ *    (component c is the velocity along axis c, in domain units per unit time).
+ *  - Interpolation extends grid data by zero outside the grid: an image or
+ *    velocity sample outside is 0 and push-forward mass that lands outside the
+ *    image grid leaves it.
+ *  - Output arrays are overwritten, never accumulated.
+ *  - All work is ordered on the context's CUDA stream; a call returns when its
+ *    work is enqueued, except where it returns host scalars (lgnk_objective,
+ *    lgnk_dot, lgnk_solve), which synchronise that stream.
+ *  - Calls return a status and never abort or throw.  A context is used by one
+ *    host thread at a time.
+ */
+#ifndef LGNK_H
+#define LGNK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LGNK_OK = 0,
+    LGNK_ERR_INVALID_ARG = 1,  /* bad pointer, size, enum value or alignment   */
+    LGNK_ERR_OOM = 2,          /* scratch does not fit the memory budget       */
+    LGNK_ERR_CUDA = 3,         /* a CUDA runtime call failed (see last error)  */
+    LGNK_ERR_NUMERIC = 4,      /* NaN or Inf met in a reduction                */
+    LGNK_ERR_INTERNAL = 5,
+    LGNK_LS_FAILED = 6,        /* Armijo found no decrease; v keeps last iterate */
+    LGNK_NOT_CONVERGED = 7     /* informational: iteration cap reached          */
+} lgnk_status;
+
+typedef enum { LGNK_TRANSPORT = 0, LGNK_CONTINUITY = 1 } lgnk_model;   /* Eq. 2 / Eq. 3 */
+typedef enum { LGNK_SSD = 0 } lgnk_distance;                           /* Eq. 10 */
+/* Sec. 2.1: diffusion (H1 seminorm), curvature (H2 seminorm); elastic is the
+ * Navier-Lame form mu |grad v|^2 + (lambda + mu)(div v)^2, which the paper names
+ * but does not define. */
+typedef enum { LGNK_DIFFUSION = 0, LGNK_CURVATURE = 1, LGNK_ELASTIC = 2 } lgnk_regularizer;
+
+/* Cell-centred regular grid (Sec. 3): d in {2, 3}; m[a] >= 1 cells on [lo[a], hi[a]]. */
+typedef struct {
+    int d;
+    int m[3];
+    double lo[3];
+    double hi[3];
+} lgnk_grid;
+
+/* The discrete problem of Eq. 9.  time_nodes = K >= 1 (the paper's n_t + 1);
+ * rk4_steps = N in [1, 64] (Alg. 1); gamma is the Hessian shift of Sec. 3.2. */
+typedef struct {
+    lgnk_grid image;
+    lgnk_grid velocity;
+    int time_nodes;
+    int rk4_steps;
+    int model;          /* lgnk_model       */
+    int distance;       /* lgnk_distance    */
+    int regularizer;    /* lgnk_regularizer */
+    double alpha;
+    double gamma;
+    double mu_lame;     /* elastic only */
+    double lambda_lame; /* elastic only */
+} lgnk_problem;
+
+typedef struct lgnk_ctx lgnk_ctx;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * legacy default stream).  mem_budget: upper bound in bytes on the scratch the
+ * context allocates (0 = no bound); LGNK_ERR_OOM when it does not fit.  The
+ * context owns its scratch (packed velocity and image copies, accumulators,
+ * FP64 reduction buffers, solver vectors) and frees it in lgnk_destroy. */
+lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budget, lgnk_ctx** out);
+void lgnk_destroy(lgnk_ctx* ctx);
+lgnk_status lgnk_set_stream(lgnk_ctx* ctx, void* stream);
+/* Bytes of device scratch this context holds. */
+size_t lgnk_scratch_bytes(const lgnk_ctx* ctx);
+const char* lgnk_status_string(lgnk_status s);
+/* Detail of the last failure on this context, or with ctx = NULL of the last
+ * failed lgnk_create on this thread (storage owned by the library, never NULL). */
+const char* lgnk_last_error(const lgnk_ctx* ctx);
+
+/* Final state u1(v) (Eq. 6 for transport, Eq. 7 for continuity).
+ * v[n], T[M] in; u1[M] out.  y: NULL, or [d][M] receiving the end points of the
+ * characteristics (transport: y(v, x_c, 1, 0); continuity: y(v, x_c, 0, 1)). */
+lgnk_status lgnk_forward(lgnk_ctx* ctx, const float* v, const float* T, float* u1, float* y);
+
+/* du = (d_v u1) dv: the derivative of the final state along dv (Sec. 3.2,
+ * derivative recursion of Alg. 1).  v[n], T[M], dv[n] in; du[M] out. */
+lgnk_status lgnk_jvp(lgnk_ctx* ctx, const float* v, const float* T, const float* dv, float* du);
+
+/* gv = (d_v u1)^T r: the transpose of lgnk_jvp.  v[n], T[M], r[M] in; gv[n] out. */
+lgnk_status lgnk_jtvp(lgnk_ctx* ctx, const float* v, const float* T, const float* r, float* gv);
+
+/* Objective of Eq. 9 with SSD (Eq. 10): J = D + alpha S, D = h^d/2 |u1 - R|^2,
+ * S = 1/2 dt h_v^d |B v|^2 (dt = 1/(K-1), 1 when stationary).  J, D, S: host
+ * doubles (each may be NULL).  grad: NULL or device [n] receiving
+ * d_v J = (d_v u1)^T h^d (u1 - R) + alpha dt h_v^d B^T B v (Sec. 3.2).
+ * Sums are accumulated in FP64.  Synchronises the stream. */
+lgnk_status lgnk_objective(lgnk_ctx* ctx, const float* v, const float* T, const float* R,
+                           double* J, double* D, double* S, float* grad);
+
+/* Gauss-Newton Hessian matvec (Sec. 3.2): Hdv = (d_v u1)^T h^d (d_v u1) dv +
+ * alpha dt h_v^d B^T B dv + gamma dv, linearised at v.  v[n], T[M], dv[n] in;
+ * Hdv[n] out. */
+lgnk_status lgnk_hessvec(lgnk_ctx* ctx, const float* v, const float* T, const float* dv, float* Hdv);
+
+/* Spectral preconditioner (Sec. 3.2): z = (alpha dt h_v^d A + gamma I)^+ r through
+ * the DCT-II eigenbasis of the Neumann operator A (zero eigenvalues act as 1;
+ * elastic uses its mu-Laplacian part).  r[n] in; z[n] out. */
+lgnk_status lgnk_precond(lgnk_ctx* ctx, const float* r, float* z);
+
+/* FP64 inner product of two device float arrays of length count; host result.
+ * Synchronises the stream. */
+lgnk_status lgnk_dot(lgnk_ctx* ctx, const float* a, const float* b, size_t count, double* out);
+
+/* Profiling.  lgnk_profile(ctx, 1) resets the counters and starts recording a
+ * pair of CUDA events on the context's stream around every tracing-kernel
+ * launch (the RK4 kernels of lgnk_forward/jvp/jtvp/objective/hessvec) and
+ * counting every kernel the context launches; lgnk_profile(ctx, 0) stops.
+ * lgnk_profile_read synchronises the stream and returns the summed tracing-
+ * kernel time in ms, the number of tracing launches and of all kernel
+ * launches since the reset (any output may be NULL). */
+lgnk_status lgnk_profile(lgnk_ctx* ctx, int enable);
+lgnk_status lgnk_profile_read(lgnk_ctx* ctx, double* trace_ms, long long* trace_launches,
+                              long long* kernel_launches);
+
+typedef struct {
+    int max_gn;           /* outer Gauss-Newton iterations (default 10)            */
+    double gn_grad_rtol;  /* stop when |g| <= rtol |g0| (default 1e-3)             */
+    int max_pcg;          /* PCG iterations per GN step (Sec. 4.1: 50)             */
+    double pcg_rtol;      /* PCG relative residual (Sec. 4.1: 0.1)                 */
+    double armijo_c;      /* sufficient-decrease constant (default 1e-4)           */
+    int max_ls;           /* Armijo halvings (default 10)                          */
+    int precond;          /* 1 = spectral preconditioner, 0 = none                 */
+    int verbosity;        /* 0 silent, 1 one line per GN iteration on stderr       */
+} lgnk_solve_opts;
+
+typedef struct {
+    int gn_iters;
+    int pcg_iters;
+    int hessvecs;
+    int objective_evals;
+    double J0, J, D, S;
+    double g0, g;
+    double seconds;
+    int status;           /* lgnk_status of the solve */
+} lgnk_solve_report;
+
+/* Fill opts with the defaults listed above. */
+void lgnk_solve_opts_default(lgnk_solve_opts* opts);
+
+/* Inexact Gauss-Newton-Krylov with Armijo line search (Eq. 11): from the
+ * initial v_inout[n] (device, overwritten with the result), minimise J for the
+ * template T[M] and reference R[M].  Hessian products, preconditioner, vector
+ * updates and FP64 inner products run on the device; the host drives the loop
+ * and reads one scalar per reduction.  opts may be NULL (defaults); report may
+ * be NULL.  Returns LGNK_OK on convergence, LGNK_NOT_CONVERGED at the GN cap,
+ * LGNK_LS_FAILED when the line search stalls. */
+lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v_inout,
+                       const lgnk_solve_opts* opts, lgnk_solve_report* report);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LGNK_H */

@@ -1,0 +1,789 @@
+// C ABI of the lgnk library (declared in include/lgnk.h): context and scratch
+// management, the hot-path entry points, and the host-driven inexact
+// Gauss-Newton-Krylov loop (Eq. 11) whose vector work and FP64 inner products
+// run on the device.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lgnk_internal.h"
+
+cudaError_t launch_trace_2d(bool nonstat, int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s);
+cudaError_t launch_trace_3d(bool nonstat, int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s);
+
+cudaError_t launch_trace(int d, bool nonstat, int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s) {
+    return d == 3 ? launch_trace_3d(nonstat, model, mode, a, nblocks, s)
+                  : launch_trace_2d(nonstat, model, mode, a, nblocks, s);
+}
+
+struct lgnk_ctx {
+    lgnk_problem prob;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t budget = 0, used = 0;
+    DevGrid ig{}, vg{};
+    int d = 0, K = 0, N = 0;
+    size_t M = 0, Mv = 0, n = 0;  // image voxels, velocity nodes per block, unknowns
+    size_t ipad = 0, vpad = 0;    // padded image elements, padded velocity nodes
+    size_t vt_bytes = 0;          // bytes of one packed velocity element
+    int tiles[3] = {1, 1, 1};
+    int trace_blocks = 0;
+    double cellvol = 0.0;         // image h^d (Eq. 10)
+    double wreg = 0.0;            // dt * h_v^d of the regularizer (Sec. 3.2)
+    void *Vp = nullptr, *dVp = nullptr, *Gp = nullptr;
+    float *Tp = nullptr, *acc = nullptr, *rp = nullptr, *itmp = nullptr, *rtmp = nullptr;
+    float *pc0 = nullptr, *pc1 = nullptr, *Cm[3] = {nullptr, nullptr, nullptr}, *inv_eig = nullptr;
+    double* partial = nullptr;
+    int npartial = 0;
+    double* dres = nullptr;
+    double* hres = nullptr;       // pinned host mirror of dres
+    float* sv[7] = {nullptr};
+    bool have_solve = false;
+    std::vector<void*> allocs;
+    // profiling: CUDA events around every tracing-kernel launch, kernel counter
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    long long launches = 0, trace_launches = 0;
+    char err[512] = {0};
+};
+
+#define SETERR(...) snprintf(ctx->err, sizeof(ctx->err), __VA_ARGS__)
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            SETERR("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);     \
+            return LGNK_ERR_CUDA;                                                                   \
+        }                                                                                           \
+    } while (0)
+// Checks a kernel launch of this library and counts it.
+#define KL(call)                                                                                    \
+    do {                                                                                            \
+        ctx->launches++;                                                                            \
+        CK(call);                                                                                   \
+    } while (0)
+#define TRY(expr)                          \
+    do {                                   \
+        lgnk_status s_ = (expr);           \
+        if (s_ != LGNK_OK) return s_;      \
+    } while (0)
+
+namespace {
+
+// Why the last lgnk_create failed (no context exists to hold it).
+thread_local char g_create_err[512] = {0};
+
+DevGrid make_grid(const lgnk_grid& g) {
+    DevGrid o{};
+    for (int a = 0; a < 3; ++a) {
+        if (a < g.d) {
+            o.m[a] = g.m[a];
+            o.mp[a] = g.m[a] + 2 * LGNK_PAD;
+            o.lo[a] = (float)g.lo[a];
+            o.h[a] = (float)((g.hi[a] - g.lo[a]) / g.m[a]);
+            o.inv_h[a] = (float)(g.m[a] / (g.hi[a] - g.lo[a]));
+        } else {
+            o.m[a] = 1;
+            o.mp[a] = 1;
+            o.lo[a] = 0.0f;
+            o.h[a] = 1.0f;
+            o.inv_h[a] = 1.0f;
+        }
+    }
+    return o;
+}
+
+const char* validate_grid(const lgnk_grid& g, int d) {
+    if (g.d != d) return "image and velocity grids must have the same dimension d";
+    for (int a = 0; a < d; ++a) {
+        if (g.m[a] < 1 || g.m[a] > (1 << 20)) return "grid cell counts must be in [1, 2^20]";
+        if (!std::isfinite(g.lo[a]) || !std::isfinite(g.hi[a]) || !(g.hi[a] > g.lo[a]))
+            return "grid bounds must be finite with hi > lo";
+    }
+    return nullptr;
+}
+
+const char* validate_problem(const lgnk_problem* p) {
+    if (p == nullptr) return "problem is NULL";
+    const int d = p->image.d;
+    if (d != 2 && d != 3) return "image.d must be 2 or 3";
+    if (const char* e = validate_grid(p->image, d)) return e;
+    if (const char* e = validate_grid(p->velocity, d)) return e;
+    if (p->time_nodes < 1 || p->time_nodes > 4096) return "time_nodes must be in [1, 4096]";
+    if (p->rk4_steps < 1 || p->rk4_steps > LGNK_MAX_STEPS) return "rk4_steps must be in [1, 64]";
+    if (p->model != LGNK_TRANSPORT && p->model != LGNK_CONTINUITY) return "unknown model";
+    if (p->distance != LGNK_SSD) return "unknown distance";
+    if (p->regularizer < LGNK_DIFFUSION || p->regularizer > LGNK_ELASTIC) return "unknown regularizer";
+    if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha)) return "alpha must be finite and >= 0";
+    if (!(p->gamma >= 0.0) || !std::isfinite(p->gamma)) return "gamma must be finite and >= 0";
+    if (p->regularizer == LGNK_ELASTIC &&
+        (!(p->mu_lame >= 0.0) || !(p->lambda_lame + p->mu_lame >= 0.0) || !std::isfinite(p->lambda_lame)))
+        return "elastic needs mu >= 0 and lambda + mu >= 0";
+    double ipad = 1.0, vpad = 1.0, M = 1.0;
+    for (int a = 0; a < d; ++a) {
+        ipad *= p->image.m[a] + 2 * LGNK_PAD;
+        vpad *= p->velocity.m[a] + 2 * LGNK_PAD;
+        M *= p->image.m[a];
+    }
+    if (ipad >= 2147483647.0 || vpad * p->time_nodes >= 2147483647.0 || M >= 2147483647.0)
+        return "grid too large for 32-bit node indexing";
+    return nullptr;
+}
+
+lgnk_status dev_alloc(lgnk_ctx* ctx, size_t bytes, void** out) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (ctx->budget != 0 && ctx->used + bytes > ctx->budget) {
+        SETERR("scratch of %zu bytes exceeds the memory budget (%zu of %zu used)", bytes, ctx->used, ctx->budget);
+        return LGNK_ERR_OOM;
+    }
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        SETERR("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return LGNK_ERR_OOM;
+    }
+    ctx->used += bytes;
+    ctx->allocs.push_back(*out);
+    return LGNK_OK;
+}
+
+template <typename T>
+lgnk_status dalloc(lgnk_ctx* ctx, size_t count, T** out) {
+    void* p = nullptr;
+    lgnk_status s = dev_alloc(ctx, count * sizeof(T), &p);
+    *out = static_cast<T*>(p);
+    return s;
+}
+
+TraceArgs base_args(const lgnk_ctx* ctx) {
+    TraceArgs a{};
+    a.ig = ctx->ig;
+    a.vg = ctx->vg;
+    a.K = ctx->K;
+    a.N = ctx->N;
+    const bool transport = ctx->prob.model == LGNK_TRANSPORT;
+    // transport traces y(v, x_c, 1, 0) backward, continuity y(v, x_c, 0, 1) forward
+    a.dt = (float)((transport ? -1.0 : 1.0) / ctx->N);
+    a.t0 = transport ? 1.0f : 0.0f;
+    a.cellvol = (float)ctx->cellvol;
+    for (int i = 0; i < 3; ++i) a.tiles[i] = ctx->tiles[i];
+    a.V = ctx->Vp;
+    a.dV = ctx->dVp;
+    a.Tp = ctx->Tp;
+    a.G = ctx->Gp;
+    return a;
+}
+
+lgnk_status record_event(lgnk_ctx* ctx) {
+    if (ctx->ev_used == ctx->ev.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->ev.push_back(e);
+    }
+    CK(cudaEventRecord(ctx->ev[ctx->ev_used++], ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status trace(lgnk_ctx* ctx, int mode, const TraceArgs& a) {
+    if (ctx->prof) TRY(record_event(ctx));
+    KL(launch_trace(ctx->d, ctx->K > 1, ctx->prob.model, mode, a, ctx->trace_blocks, ctx->stream));
+    ctx->trace_launches++;
+    if (ctx->prof) TRY(record_event(ctx));
+    return LGNK_OK;
+}
+
+lgnk_status pack_v(lgnk_ctx* ctx, const float* v, void* dst) {
+    KL(launch_pack_velocity(ctx->d, v, dst, ctx->vg, ctx->K, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status pack_T(lgnk_ctx* ctx, const float* T) {
+    KL(launch_pack_image(T, ctx->Tp, ctx->ig, ctx->d, 1.0f, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status zero_G(lgnk_ctx* ctx) {
+    CK(cudaMemsetAsync(ctx->Gp, 0, ctx->vpad * ctx->K * ctx->vt_bytes, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status zero_acc(lgnk_ctx* ctx) {
+    CK(cudaMemsetAsync(ctx->acc, 0, ctx->ipad * sizeof(float), ctx->stream));
+    return LGNK_OK;
+}
+
+// out = addsrc + scale * A_reg x + gamma * x (A_reg the regularizer's operator).
+// x must not alias out; addsrc may equal out.
+lgnk_status reg_apply(lgnk_ctx* ctx, const float* x, float* out, double scale, double gamma, const float* addsrc) {
+    const int kd = ctx->K * ctx->d;
+    switch (ctx->prob.regularizer) {
+        case LGNK_DIFFUSION:
+            KL(launch_laplacian(ctx->d, x, out, ctx->vg, kd, (float)scale, (float)gamma, addsrc, ctx->stream));
+            break;
+        case LGNK_CURVATURE:
+            KL(launch_laplacian(ctx->d, x, ctx->rtmp, ctx->vg, kd, 1.0f, 0.0f, nullptr, ctx->stream));
+            KL(launch_laplacian_ext(ctx->d, ctx->rtmp, out, ctx->vg, kd, (float)scale, (float)gamma,
+                                    gamma != 0.0 ? x : nullptr, addsrc, ctx->stream));
+            break;
+        case LGNK_ELASTIC:
+            KL(launch_divergence(ctx->d, x, ctx->rtmp, ctx->vg, ctx->K, ctx->stream));
+            KL(launch_elastic(ctx->d, x, ctx->rtmp, out, ctx->vg, ctx->K, (float)(scale * ctx->prob.mu_lame),
+                              (float)(scale * (ctx->prob.lambda_lame + ctx->prob.mu_lame)), (float)gamma, addsrc,
+                              ctx->stream));
+            break;
+        default:
+            SETERR("unknown regularizer");
+            return LGNK_ERR_INTERNAL;
+    }
+    return LGNK_OK;
+}
+
+lgnk_status fetch(lgnk_ctx* ctx, int count) {
+    CK(cudaMemcpyAsync(ctx->hres, ctx->dres, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status dot_dev(lgnk_ctx* ctx, const float* a, const float* b, size_t count, int slot) {
+    const int nb = dot_blocks(count);
+    KL(launch_dot(a, b, count, ctx->partial, nb, ctx->stream));
+    KL(launch_reduce(ctx->partial, nb, ctx->dres + slot, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status dot_host(lgnk_ctx* ctx, const float* a, const float* b, size_t count, double* out) {
+    TRY(dot_dev(ctx, a, b, count, 2));
+    TRY(fetch(ctx, 3));
+    *out = ctx->hres[2];
+    if (!std::isfinite(*out)) {
+        SETERR("non-finite inner product");
+        return LGNK_ERR_NUMERIC;
+    }
+    return LGNK_OK;
+}
+
+// ---- internal operations: velocity already packed in Vp (and template in Tp) ----
+
+lgnk_status forward_packed(lgnk_ctx* ctx, const float* T, float* u1, float* y) {
+    TraceArgs a = base_args(ctx);
+    a.yout = y;
+    if (ctx->prob.model == LGNK_TRANSPORT) {
+        a.u1 = u1;
+        return trace(ctx, MODE_FWD, a);
+    }
+    TRY(zero_acc(ctx));
+    a.T = T;
+    a.acc = ctx->acc;
+    TRY(trace(ctx, MODE_FWD, a));
+    KL(launch_unpack_image(ctx->acc, u1, ctx->ig, ctx->d, ctx->stream));
+    return LGNK_OK;
+}
+
+// J, D, S at the packed velocity; v is the same velocity in ABI layout (for S).
+lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, const float* R, float* grad,
+                             double* J, double* D, double* S) {
+    TraceArgs a = base_args(ctx);
+    a.R = R;
+    a.partial = ctx->partial;
+    int nred = ctx->trace_blocks;
+    if (ctx->prob.model == LGNK_TRANSPORT) {
+        if (grad != nullptr) {
+            TRY(zero_G(ctx));
+            TRY(trace(ctx, MODE_OBJGRAD, a));
+        } else {
+            a.u1 = ctx->itmp;
+            TRY(trace(ctx, MODE_FWD, a));
+        }
+    } else {
+        TRY(zero_acc(ctx));
+        TraceArgs f = base_args(ctx);
+        f.T = T;
+        f.acc = ctx->acc;
+        TRY(trace(ctx, MODE_FWD, f));
+        KL(launch_unpack_image(ctx->acc, ctx->itmp, ctx->ig, ctx->d, ctx->stream));
+        nred = residual_blocks(ctx->ig, ctx->d);
+        KL(launch_residual(ctx->itmp, R, ctx->rp, ctx->ig, ctx->d, (float)ctx->cellvol, ctx->partial, nred,
+                           ctx->stream));
+        if (grad != nullptr) {
+            TRY(zero_G(ctx));
+            TraceArgs b = base_args(ctx);
+            b.T = T;
+            b.r = ctx->rp;
+            TRY(trace(ctx, MODE_JTVP, b));
+        }
+    }
+    KL(launch_reduce(ctx->partial, nred, ctx->dres + 0, ctx->stream));
+    if (grad != nullptr) {
+        KL(launch_unpack_velocity(ctx->d, ctx->Gp, grad, ctx->vg, ctx->K, 1.0f, ctx->stream));
+        TRY(reg_apply(ctx, v, grad, ctx->prob.alpha * ctx->wreg, 0.0, grad));
+    }
+    // S = 1/2 dt h_v^d v^T A_reg v
+    TRY(reg_apply(ctx, v, ctx->pc0, 1.0, 0.0, nullptr));
+    TRY(dot_dev(ctx, v, ctx->pc0, ctx->n, 1));
+    TRY(fetch(ctx, 2));
+    const double Dv = 0.5 * ctx->cellvol * ctx->hres[0];
+    const double Sv = 0.5 * ctx->wreg * ctx->hres[1];
+    if (!std::isfinite(Dv) || !std::isfinite(Sv)) {
+        SETERR("non-finite objective");
+        return LGNK_ERR_NUMERIC;
+    }
+    if (D) *D = Dv;
+    if (S) *S = Sv;
+    if (J) *J = Dv + ctx->prob.alpha * Sv;
+    return LGNK_OK;
+}
+
+// out = J^T h^d J dv + alpha dt h_v^d A dv + gamma dv at the packed velocity.
+lgnk_status hessvec_packed(lgnk_ctx* ctx, const float* T, const float* dv, float* out) {
+    TRY(pack_v(ctx, dv, ctx->dVp));
+    TRY(zero_G(ctx));
+    if (ctx->prob.model == LGNK_TRANSPORT) {
+        TraceArgs a = base_args(ctx);
+        TRY(trace(ctx, MODE_HESS, a));
+    } else {
+        TRY(zero_acc(ctx));
+        TraceArgs a = base_args(ctx);
+        a.T = T;
+        a.acc = ctx->acc;
+        TRY(trace(ctx, MODE_JVP, a));
+        KL(launch_repad_image(ctx->acc, ctx->ig, ctx->d, (float)ctx->cellvol, ctx->stream));
+        TraceArgs b = base_args(ctx);
+        b.T = T;
+        b.r = ctx->acc;
+        TRY(trace(ctx, MODE_JTVP, b));
+    }
+    KL(launch_unpack_velocity(ctx->d, ctx->Gp, out, ctx->vg, ctx->K, 1.0f, ctx->stream));
+    return reg_apply(ctx, dv, out, ctx->prob.alpha * ctx->wreg, ctx->prob.gamma, out);
+}
+
+lgnk_status precond_apply(lgnk_ctx* ctx, const float* r, float* z) {
+    const int kd = ctx->K * ctx->d;
+    cudaStream_t s = ctx->stream;
+    if (ctx->d == 3) {
+        KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 3, kd, 0, false, s));
+        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, false, s));
+        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[2], ctx->vg, 3, kd, 2, false, s));
+        KL(launch_scale_modes(ctx->pc0, ctx->inv_eig, ctx->Mv, ctx->n, s));
+        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[2], ctx->vg, 3, kd, 2, true, s));
+        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[1], ctx->vg, 3, kd, 1, true, s));
+        KL(launch_dct_axis(ctx->pc0, z, ctx->Cm[0], ctx->vg, 3, kd, 0, true, s));
+    } else {
+        KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 2, kd, 0, false, s));
+        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 2, kd, 1, false, s));
+        KL(launch_scale_modes(ctx->pc1, ctx->inv_eig, ctx->Mv, ctx->n, s));
+        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[1], ctx->vg, 2, kd, 1, true, s));
+        KL(launch_dct_axis(ctx->pc0, z, ctx->Cm[0], ctx->vg, 2, kd, 0, true, s));
+    }
+    return LGNK_OK;
+}
+
+bool distinct(const void* out, std::initializer_list<const void*> ins) {
+    for (const void* p : ins)
+        if (p != nullptr && p == out) return false;
+    return true;
+}
+
+}  // namespace
+
+#define CHECK_CTX()                                                  \
+    do {                                                             \
+        if (ctx == nullptr) return LGNK_ERR_INVALID_ARG;             \
+    } while (0)
+#define REQUIRE(cond, msg)                                           \
+    do {                                                             \
+        if (!(cond)) {                                               \
+            SETERR("%s", msg);                                       \
+            return LGNK_ERR_INVALID_ARG;                             \
+        }                                                            \
+    } while (0)
+
+extern "C" {
+
+const char* lgnk_status_string(lgnk_status s) {
+    switch (s) {
+        case LGNK_OK: return "ok";
+        case LGNK_ERR_INVALID_ARG: return "invalid argument";
+        case LGNK_ERR_OOM: return "out of memory (budget or device)";
+        case LGNK_ERR_CUDA: return "CUDA error";
+        case LGNK_ERR_NUMERIC: return "non-finite value";
+        case LGNK_ERR_INTERNAL: return "internal error";
+        case LGNK_LS_FAILED: return "line search failed";
+        case LGNK_NOT_CONVERGED: return "not converged (iteration cap)";
+    }
+    return "unknown status";
+}
+
+const char* lgnk_last_error(const lgnk_ctx* ctx) {
+    return ctx == nullptr ? g_create_err : ctx->err;
+}
+
+size_t lgnk_scratch_bytes(const lgnk_ctx* ctx) {
+    return ctx == nullptr ? 0 : ctx->used;
+}
+
+void lgnk_destroy(lgnk_ctx* ctx) {
+    if (ctx == nullptr) return;
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->hres) cudaFreeHost(ctx->hres);
+    delete ctx;
+}
+
+lgnk_status lgnk_set_stream(lgnk_ctx* ctx, void* stream) {
+    CHECK_CTX();
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budget, lgnk_ctx** out) {
+    g_create_err[0] = 0;
+    if (out == nullptr) return LGNK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (const char* e = validate_problem(prob)) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", e);
+        return LGNK_ERR_INVALID_ARG;
+    }
+    lgnk_ctx* ctx = new (std::nothrow) lgnk_ctx();
+    if (ctx == nullptr) return LGNK_ERR_OOM;
+    ctx->prob = *prob;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->budget = mem_budget;
+    const int d = prob->image.d;
+    ctx->d = d;
+    ctx->K = prob->time_nodes;
+    ctx->N = prob->rk4_steps;
+    ctx->ig = make_grid(prob->image);
+    ctx->vg = make_grid(prob->velocity);
+    ctx->M = (size_t)ctx->ig.m[0] * ctx->ig.m[1] * ctx->ig.m[2];
+    ctx->Mv = (size_t)ctx->vg.m[0] * ctx->vg.m[1] * ctx->vg.m[2];
+    ctx->n = ctx->Mv * d * ctx->K;
+    ctx->ipad = (size_t)ctx->ig.mp[0] * ctx->ig.mp[1] * ctx->ig.mp[2];
+    ctx->vpad = (size_t)ctx->vg.mp[0] * ctx->vg.mp[1] * ctx->vg.mp[2];
+    ctx->vt_bytes = d == 3 ? 16 : 8;
+    const int tx = d == 3 ? 8 : 16, ty = d == 3 ? 8 : 16, tz = d == 3 ? 4 : 1;
+    ctx->tiles[0] = (ctx->ig.m[0] + tx - 1) / tx;
+    ctx->tiles[1] = (ctx->ig.m[1] + ty - 1) / ty;
+    ctx->tiles[2] = (ctx->ig.m[2] + tz - 1) / tz;
+    ctx->trace_blocks = ctx->tiles[0] * ctx->tiles[1] * ctx->tiles[2];
+    double hv = 1.0, hi = 1.0;
+    for (int a = 0; a < d; ++a) {
+        hi *= (prob->image.hi[a] - prob->image.lo[a]) / prob->image.m[a];
+        hv *= (prob->velocity.hi[a] - prob->velocity.lo[a]) / prob->velocity.m[a];
+    }
+    ctx->cellvol = hi;
+    ctx->wreg = (ctx->K == 1 ? 1.0 : 1.0 / (ctx->K - 1)) * hv;
+
+    auto fail = [&](lgnk_status s) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", ctx->err[0] ? ctx->err : lgnk_status_string(s));
+        lgnk_destroy(ctx);
+        return s;
+    };
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LGNK_ERR_CUDA);
+    }
+    const size_t vbytes = ctx->vpad * ctx->K * ctx->vt_bytes;
+    lgnk_status s;
+    if ((s = dev_alloc(ctx, vbytes, &ctx->Vp)) != LGNK_OK) return fail(s);
+    if ((s = dev_alloc(ctx, vbytes, &ctx->dVp)) != LGNK_OK) return fail(s);
+    if ((s = dev_alloc(ctx, vbytes, &ctx->Gp)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, ctx->ipad, &ctx->Tp)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, ctx->ipad, &ctx->acc)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, ctx->M, &ctx->itmp)) != LGNK_OK) return fail(s);
+    if (prob->model == LGNK_CONTINUITY) {
+        if ((s = dalloc(ctx, ctx->ipad, &ctx->rp)) != LGNK_OK) return fail(s);
+    }
+    if ((s = dalloc(ctx, ctx->n, &ctx->rtmp)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, ctx->n, &ctx->pc0)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, ctx->n, &ctx->pc1)) != LGNK_OK) return fail(s);
+    for (int a = 0; a < d; ++a)
+        if ((s = dalloc(ctx, (size_t)ctx->vg.m[a] * ctx->vg.m[a], &ctx->Cm[a])) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, ctx->Mv, &ctx->inv_eig)) != LGNK_OK) return fail(s);
+    ctx->npartial = ctx->trace_blocks > 1024 ? ctx->trace_blocks : 1024;
+    if ((s = dalloc(ctx, (size_t)ctx->npartial, &ctx->partial)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, 8, &ctx->dres)) != LGNK_OK) return fail(s);
+    if (cudaMallocHost((void**)&ctx->hres, 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->hres = nullptr;
+        return fail(LGNK_ERR_OOM);
+    }
+
+    // Spectral preconditioner tables (Sec. 3.2): orthonormal DCT-II per axis and
+    // the inverse eigenvalues of alpha dt h_v^d A_reg + gamma I (zero -> 1).
+    std::vector<float> hostC;
+    for (int a = 0; a < d; ++a) {
+        const int m = ctx->vg.m[a];
+        hostC.assign((size_t)m * m, 0.0f);
+        for (int k = 0; k < m; ++k)
+            for (int i = 0; i < m; ++i)
+                hostC[(size_t)k * m + i] =
+                    (float)(std::sqrt((k == 0 ? 1.0 : 2.0) / m) * std::cos(M_PI * k * (2 * i + 1) / (2.0 * m)));
+        if (cudaMemcpy(ctx->Cm[a], hostC.data(), hostC.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(LGNK_ERR_CUDA);
+    }
+    std::vector<float> ev(ctx->Mv);
+    const double wa = prob->alpha * ctx->wreg;
+    for (size_t sidx = 0; sidx < ctx->Mv; ++sidx) {
+        size_t r = sidx;
+        double lam = 0.0;
+        for (int a = 0; a < d; ++a) {
+            const int m = prob->velocity.m[a];
+            const int k = (int)(r % m);
+            r /= m;
+            const double h = (prob->velocity.hi[a] - prob->velocity.lo[a]) / m;
+            lam += (2.0 - 2.0 * std::cos(M_PI * k / m)) / (h * h);
+        }
+        if (prob->regularizer == LGNK_CURVATURE) lam = lam * lam;
+        if (prob->regularizer == LGNK_ELASTIC) lam = prob->mu_lame * lam;
+        const double p = wa * lam + prob->gamma;
+        ev[sidx] = (float)(p == 0.0 ? 1.0 : 1.0 / p);
+    }
+    if (cudaMemcpy(ctx->inv_eig, ev.data(), ev.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LGNK_ERR_CUDA);
+    if (ctx->rp && cudaMemset(ctx->rp, 0, ctx->ipad * sizeof(float)) != cudaSuccess) return fail(LGNK_ERR_CUDA);
+    *out = ctx;
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_forward(lgnk_ctx* ctx, const float* v, const float* T, float* u1, float* y) {
+    CHECK_CTX();
+    REQUIRE(v && T && u1, "v, T and u1 must be non-NULL");
+    REQUIRE(distinct(u1, {v, T}) && distinct(y, {v, T, u1}), "outputs must not alias inputs");
+    TRY(pack_v(ctx, v, ctx->Vp));
+    if (ctx->prob.model == LGNK_TRANSPORT) TRY(pack_T(ctx, T));
+    return forward_packed(ctx, T, u1, y);
+}
+
+lgnk_status lgnk_jvp(lgnk_ctx* ctx, const float* v, const float* T, const float* dv, float* du) {
+    CHECK_CTX();
+    REQUIRE(v && T && dv && du, "v, T, dv and du must be non-NULL");
+    REQUIRE(distinct(du, {v, T, dv}), "outputs must not alias inputs");
+    TRY(pack_v(ctx, v, ctx->Vp));
+    TRY(pack_v(ctx, dv, ctx->dVp));
+    TraceArgs a = base_args(ctx);
+    if (ctx->prob.model == LGNK_TRANSPORT) {
+        TRY(pack_T(ctx, T));
+        a.u1 = du;
+        return trace(ctx, MODE_JVP, a);
+    }
+    TRY(zero_acc(ctx));
+    a.T = T;
+    a.acc = ctx->acc;
+    TRY(trace(ctx, MODE_JVP, a));
+    KL(launch_unpack_image(ctx->acc, du, ctx->ig, ctx->d, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_jtvp(lgnk_ctx* ctx, const float* v, const float* T, const float* r, float* gv) {
+    CHECK_CTX();
+    REQUIRE(v && T && r && gv, "v, T, r and gv must be non-NULL");
+    REQUIRE(distinct(gv, {v, T, r}), "outputs must not alias inputs");
+    TRY(pack_v(ctx, v, ctx->Vp));
+    TRY(zero_G(ctx));
+    TraceArgs a = base_args(ctx);
+    if (ctx->prob.model == LGNK_TRANSPORT) {
+        TRY(pack_T(ctx, T));
+        a.r = r;
+    } else {
+        KL(launch_pack_image(r, ctx->rp, ctx->ig, ctx->d, 1.0f, ctx->stream));
+        a.T = T;
+        a.r = ctx->rp;
+    }
+    TRY(trace(ctx, MODE_JTVP, a));
+    KL(launch_unpack_velocity(ctx->d, ctx->Gp, gv, ctx->vg, ctx->K, 1.0f, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_objective(lgnk_ctx* ctx, const float* v, const float* T, const float* R, double* J, double* D,
+                           double* S, float* grad) {
+    CHECK_CTX();
+    REQUIRE(v && T && R, "v, T and R must be non-NULL");
+    REQUIRE(distinct(grad, {v, T, R}), "outputs must not alias inputs");
+    TRY(pack_v(ctx, v, ctx->Vp));
+    if (ctx->prob.model == LGNK_TRANSPORT) TRY(pack_T(ctx, T));
+    return objective_packed(ctx, v, T, R, grad, J, D, S);
+}
+
+lgnk_status lgnk_hessvec(lgnk_ctx* ctx, const float* v, const float* T, const float* dv, float* Hdv) {
+    CHECK_CTX();
+    REQUIRE(v && T && dv && Hdv, "v, T, dv and Hdv must be non-NULL");
+    REQUIRE(distinct(Hdv, {v, T, dv}), "outputs must not alias inputs");
+    TRY(pack_v(ctx, v, ctx->Vp));
+    if (ctx->prob.model == LGNK_TRANSPORT) TRY(pack_T(ctx, T));
+    return hessvec_packed(ctx, T, dv, Hdv);
+}
+
+lgnk_status lgnk_precond(lgnk_ctx* ctx, const float* r, float* z) {
+    CHECK_CTX();
+    REQUIRE(r && z, "r and z must be non-NULL");
+    return precond_apply(ctx, r, z);
+}
+
+lgnk_status lgnk_dot(lgnk_ctx* ctx, const float* a, const float* b, size_t count, double* out) {
+    CHECK_CTX();
+    REQUIRE(a && b && out, "a, b and out must be non-NULL");
+    if (count == 0) {
+        *out = 0.0;
+        return LGNK_OK;
+    }
+    return dot_host(ctx, a, b, count, out);
+}
+
+lgnk_status lgnk_profile(lgnk_ctx* ctx, int enable) {
+    CHECK_CTX();
+    ctx->prof = enable != 0;
+    ctx->ev_used = 0;
+    ctx->launches = 0;
+    ctx->trace_launches = 0;
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_profile_read(lgnk_ctx* ctx, double* trace_ms, long long* trace_launches,
+                              long long* kernel_launches) {
+    CHECK_CTX();
+    CK(cudaStreamSynchronize(ctx->stream));
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+        total += ms;
+    }
+    if (trace_ms) *trace_ms = total;
+    if (trace_launches) *trace_launches = ctx->trace_launches;
+    if (kernel_launches) *kernel_launches = ctx->launches;
+    return LGNK_OK;
+}
+
+void lgnk_solve_opts_default(lgnk_solve_opts* o) {
+    if (o == nullptr) return;
+    o->max_gn = 10;
+    o->gn_grad_rtol = 1e-3;
+    o->max_pcg = 50;
+    o->pcg_rtol = 0.1;
+    o->armijo_c = 1e-4;
+    o->max_ls = 10;
+    o->precond = 1;
+    o->verbosity = 0;
+}
+
+lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts* opts_in,
+                       lgnk_solve_report* rep_out) {
+    CHECK_CTX();
+    REQUIRE(T && R && v, "T, R and v_inout must be non-NULL");
+    REQUIRE(distinct(v, {T, R}), "v_inout must not alias T or R");
+    lgnk_solve_opts o;
+    lgnk_solve_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    REQUIRE(o.max_gn >= 0 && o.max_pcg >= 1 && o.max_ls >= 1 && o.pcg_rtol > 0.0 && o.gn_grad_rtol >= 0.0,
+            "invalid solve options");
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!ctx->have_solve) {
+        for (int i = 0; i < 7; ++i) TRY(dalloc(ctx, ctx->n, &ctx->sv[i]));
+        ctx->have_solve = true;
+    }
+    float *x = ctx->sv[0], *r = ctx->sv[1], *z = ctx->sv[2], *p = ctx->sv[3], *Hp = ctx->sv[4], *g = ctx->sv[5],
+          *vt = ctx->sv[6];
+    const size_t n = ctx->n;
+    cudaStream_t s = ctx->stream;
+    lgnk_solve_report rep;
+    memset(&rep, 0, sizeof(rep));
+
+    if (ctx->prob.model == LGNK_TRANSPORT) TRY(pack_T(ctx, T));
+    TRY(pack_v(ctx, v, ctx->Vp));
+    double J, D, S;
+    TRY(objective_packed(ctx, v, T, R, g, &J, &D, &S));
+    rep.objective_evals = 1;
+    double gg;
+    TRY(dot_host(ctx, g, g, n, &gg));
+    const double g0 = std::sqrt(gg);
+    rep.J0 = J;
+    rep.g0 = g0;
+    lgnk_status status = LGNK_NOT_CONVERGED;
+    double gn = g0;
+    for (int it = 0; it < o.max_gn; ++it) {
+        if (gn <= o.gn_grad_rtol * g0) {
+            status = LGNK_OK;
+            break;
+        }
+        // PCG on H x = -g from x = 0 (Eq. 11)
+        CK(cudaMemsetAsync(x, 0, n * sizeof(float), s));
+        KL(launch_add_scaled(r, g, -1.0f, g, 0.0f, n, s));
+        if (o.precond) TRY(precond_apply(ctx, r, z));
+        else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(p, z, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        double rz;
+        TRY(dot_host(ctx, r, z, n, &rz));
+        int pit = 0;
+        for (int i = 1; i <= o.max_pcg; ++i) {
+            TRY(hessvec_packed(ctx, T, p, Hp));
+            rep.hessvecs++;
+            double pHp;
+            TRY(dot_host(ctx, p, Hp, n, &pHp));
+            if (!(pHp > 0.0)) {
+                if (pit == 0) CK(cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+                break;
+            }
+            const double a = rz / pHp;
+            KL(launch_axpby((float)a, p, 1.0f, x, n, s));
+            KL(launch_axpby((float)-a, Hp, 1.0f, r, n, s));
+            pit = i;
+            double rr;
+            TRY(dot_host(ctx, r, r, n, &rr));
+            if (std::sqrt(rr) <= o.pcg_rtol * gn) break;
+            if (o.precond) TRY(precond_apply(ctx, r, z));
+            else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            double rzn;
+            TRY(dot_host(ctx, r, z, n, &rzn));
+            KL(launch_axpby(1.0f, z, (float)(rzn / rz), p, n, s));
+            rz = rzn;
+        }
+        rep.pcg_iters += pit;
+        // Armijo backtracking on v + mu x (FP64 comparisons)
+        double slope;
+        TRY(dot_host(ctx, g, x, n, &slope));
+        double mu = 1.0, Jt = J;
+        bool accepted = false;
+        for (int ls = 0; ls < o.max_ls; ++ls) {
+            KL(launch_add_scaled(vt, v, 1.0f, x, (float)mu, n, s));
+            TRY(pack_v(ctx, vt, ctx->Vp));
+            TRY(objective_packed(ctx, vt, T, R, nullptr, &Jt, nullptr, nullptr));
+            rep.objective_evals++;
+            if (Jt <= J + o.armijo_c * mu * slope) {
+                accepted = true;
+                break;
+            }
+            mu *= 0.5;
+        }
+        rep.gn_iters = it + 1;
+        if (!accepted) {
+            TRY(pack_v(ctx, v, ctx->Vp));
+            status = LGNK_LS_FAILED;
+            break;
+        }
+        CK(cudaMemcpyAsync(v, vt, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        TRY(objective_packed(ctx, v, T, R, g, &J, &D, &S));
+        rep.objective_evals++;
+        TRY(dot_host(ctx, g, g, n, &gg));
+        gn = std::sqrt(gg);
+        if (o.verbosity > 0)
+            fprintf(stderr, "lgnk GN %3d  J %.6e  D %.6e  S %.6e  |g|/|g0| %.3e  pcg %d  mu %.3g\n", it + 1, J, D,
+                    S, gn / g0, pit, mu);
+    }
+    if (status == LGNK_NOT_CONVERGED && gn <= o.gn_grad_rtol * g0) status = LGNK_OK;
+    CK(cudaStreamSynchronize(s));
+    rep.J = J;
+    rep.D = D;
+    rep.S = S;
+    rep.g = gn;
+    rep.status = status;
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (rep_out) *rep_out = rep;
+    return status;
+}
+
+}  // extern "C"

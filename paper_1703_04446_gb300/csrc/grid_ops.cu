@@ -1,0 +1,423 @@
+// Grid utilities of the lgnk library: layout conversion between the ABI layout
+// and the padded packed layout of the tracing kernels, FP64 reductions,
+// regularizer stencils (Sec. 2.1, Sec. 3.2), the per-axis DCT of the spectral
+// preconditioner (Sec. 3.2) and the vector updates of PCG.
+#include "lgnk_internal.h"
+
+namespace {
+
+constexpr int kBlock = LGNK_BLOCK;
+constexpr int kReduceBlocks = 608;  // 4 x 152 SMs for grid-stride reductions
+
+inline int nblocks_for(size_t count) {
+    return (int)((count + kBlock - 1) / kBlock);
+}
+
+__device__ __forceinline__ size_t padded_size(const DevGrid& g) {
+    return (size_t)g.mp[0] * g.mp[1] * g.mp[2];
+}
+
+// ---------------------------------------------------------------- packing --
+
+template <int D>
+__global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restrict__ Vp, DevGrid g, int K) {
+    const size_t total = padded_size(g) * K;
+    const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    constexpr int W = (D == 3) ? 4 : 2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % K);
+        const size_t node = i / K;
+        const int px = (int)(node % g.mp[0]);
+        const int py = (int)((node / g.mp[0]) % g.mp[1]);
+        const int pz = (int)(node / ((size_t)g.mp[0] * g.mp[1]));
+        const int x = px - LGNK_PAD, y = py - LGNK_PAD, z = (D == 3) ? pz - LGNK_PAD : 0;
+        const bool in = x >= 0 && x < g.m[0] && y >= 0 && y < g.m[1] && z >= 0 && z < g.m[2];
+        float out[4] = {0.f, 0.f, 0.f, 0.f};
+        if (in) {
+            const size_t s = ((size_t)z * g.m[1] + y) * g.m[0] + x;
+#pragma unroll
+            for (int c = 0; c < D; ++c) out[c] = v[((size_t)j * D + c) * Mv + s];
+        }
+        if (W == 4) reinterpret_cast<float4*>(Vp)[i] = make_float4(out[0], out[1], out[2], 0.f);
+        else reinterpret_cast<float2*>(Vp)[i] = make_float2(out[0], out[1]);
+    }
+}
+
+template <int D>
+__global__ void unpack_velocity_kernel(const float* __restrict__ Gp, float* __restrict__ out, DevGrid g, int K,
+                                       float scale) {
+    const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t total = Mv * K;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = i % Mv;
+        const int j = (int)(i / Mv);
+        const int x = (int)(s % g.m[0]);
+        const int y = (int)((s / g.m[0]) % g.m[1]);
+        const int z = (int)(s / ((size_t)g.m[0] * g.m[1]));
+        const size_t node = ((size_t)(z + (D == 3 ? LGNK_PAD : 0)) * g.mp[1] + (y + LGNK_PAD)) * g.mp[0] + (x + LGNK_PAD);
+        const size_t e = node * K + j;
+        float val[4];
+        if (D == 3) {
+            const float4 a = reinterpret_cast<const float4*>(Gp)[e];
+            val[0] = a.x; val[1] = a.y; val[2] = a.z;
+        } else {
+            const float2 a = reinterpret_cast<const float2*>(Gp)[e];
+            val[0] = a.x; val[1] = a.y;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[((size_t)j * D + c) * Mv + s] = scale * val[c];
+    }
+}
+
+__global__ void pack_image_kernel(const float* __restrict__ T, float* __restrict__ Tp, DevGrid g, int d, float scale) {
+    const size_t total = padded_size(g);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int px = (int)(i % g.mp[0]);
+        const int py = (int)((i / g.mp[0]) % g.mp[1]);
+        const int pz = (int)(i / ((size_t)g.mp[0] * g.mp[1]));
+        const int x = px - LGNK_PAD, y = py - LGNK_PAD, z = (d == 3) ? pz - LGNK_PAD : 0;
+        const bool in = x >= 0 && x < g.m[0] && y >= 0 && y < g.m[1] && z >= 0 && z < g.m[2];
+        Tp[i] = in ? scale * T[((size_t)z * g.m[1] + y) * g.m[0] + x] : 0.0f;
+    }
+}
+
+__global__ void unpack_image_kernel(const float* __restrict__ acc, float* __restrict__ out, DevGrid g, int d) {
+    const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.m[0]);
+        const int y = (int)((i / g.m[0]) % g.m[1]);
+        const int z = (int)(i / ((size_t)g.m[0] * g.m[1]));
+        const size_t p = ((size_t)(z + (d == 3 ? LGNK_PAD : 0)) * g.mp[1] + (y + LGNK_PAD)) * g.mp[0] + (x + LGNK_PAD);
+        out[i] = acc[p];
+    }
+}
+
+__global__ void repad_image_kernel(float* acc, DevGrid g, int d, float scale) {
+    const size_t total = padded_size(g);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int px = (int)(i % g.mp[0]);
+        const int py = (int)((i / g.mp[0]) % g.mp[1]);
+        const int pz = (int)(i / ((size_t)g.mp[0] * g.mp[1]));
+        const int x = px - LGNK_PAD, y = py - LGNK_PAD, z = (d == 3) ? pz - LGNK_PAD : 0;
+        const bool in = x >= 0 && x < g.m[0] && y >= 0 && y < g.m[1] && z >= 0 && z < g.m[2];
+        acc[i] = in ? scale * acc[i] : 0.0f;
+    }
+}
+
+// ------------------------------------------------------------- reductions --
+
+__device__ __forceinline__ double block_reduce(double x) {
+    __shared__ double red[kBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    double s = 0.0;
+    if (warp == 0) {
+        s = (lane < kBlock / 32) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+// res = u1 - R (Eq. 10): FP64 partial sums of res^2 per block; rp (padded) = scale * res.
+__global__ void residual_kernel(const float* __restrict__ u1, const float* __restrict__ R, float* __restrict__ rp,
+                                DevGrid g, int d, float scale, double* partial) {
+    const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+        const float r = u1[i] - R[i];
+        s += (double)r * (double)r;
+        if (rp != nullptr) {
+            const int x = (int)(i % g.m[0]);
+            const int y = (int)((i / g.m[0]) % g.m[1]);
+            const int z = (int)(i / ((size_t)g.m[0] * g.m[1]));
+            const size_t p = ((size_t)(z + (d == 3 ? LGNK_PAD : 0)) * g.mp[1] + (y + LGNK_PAD)) * g.mp[0] + (x + LGNK_PAD);
+            rp[p] = scale * r;
+        }
+    }
+    s = block_reduce(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b, size_t count, double* partial) {
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)b[i];
+    s = block_reduce(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// Deterministic final sum of the per-block partials (one block).
+__global__ void reduce_kernel(const double* __restrict__ partial, int count, double* out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += partial[i];
+    s = block_reduce(s);
+    if (threadIdx.x == 0) out[0] = s;
+}
+
+// ----------------------------------------------------------- regularizers --
+
+template <int D>
+__device__ __forceinline__ void coords(size_t s, const DevGrid& g, int* c) {
+    c[0] = (int)(s % g.m[0]);
+    c[1] = (int)((s / g.m[0]) % g.m[1]);
+    c[2] = (D == 3) ? (int)(s / ((size_t)g.m[0] * g.m[1])) : 0;
+}
+
+// out = addsrc + scale * (B^T B x) + gamma * gsrc: the Neumann Laplacian of each
+// (time node, component) block, B the forward difference between neighbouring
+// cell centres (interior faces only).
+template <int D>
+__global__ void laplacian_kernel(const float* __restrict__ x, float* out, DevGrid g, int nblk, float scale,
+                                 float gamma, const float* gsrc, const float* addsrc) {
+    const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t total = Mv * nblk;
+    const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = i % Mv;
+        int c[3];
+        coords<D>(s, g, c);
+        const float xi = x[i];
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            float t = 0.0f;
+            if (c[a] > 0) t += xi - x[i - stride[a]];
+            if (c[a] < g.m[a] - 1) t += xi - x[i + stride[a]];
+            acc = fmaf(t, g.inv_h[a] * g.inv_h[a], acc);
+        }
+        float r = scale * acc;
+        if (gsrc != nullptr) r = fmaf(gamma, gsrc[i], r);
+        if (addsrc != nullptr) r += addsrc[i];
+        out[i] = r;
+    }
+}
+
+// div[j] = sum_a (x_a[i+1] - x_a[i-1]) / (2 h_a), ends mirrored (one-sided).
+template <int D>
+__global__ void divergence_kernel(const float* __restrict__ x, float* __restrict__ div, DevGrid g, int K) {
+    const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t total = Mv * K;
+    const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = i % Mv;
+        const size_t j = i / Mv;
+        int c[3];
+        coords<D>(s, g, c);
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const float* xa = x + (j * D + a) * Mv;
+            const size_t up = (c[a] < g.m[a] - 1) ? s + stride[a] : s;
+            const size_t dn = (c[a] > 0) ? s - stride[a] : s;
+            acc += (xa[up] - xa[dn]) * (0.5f * g.inv_h[a]);
+        }
+        div[i] = acc;
+    }
+}
+
+// out_c = addsrc + smu * (A x_c) + slm * (D_c^T div) + gamma * x_c (elastic operator).
+template <int D>
+__global__ void elastic_kernel(const float* __restrict__ x, const float* __restrict__ div, float* out, DevGrid g,
+                               int K, float smu, float slm, float gamma, const float* addsrc) {
+    const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t total = Mv * K * D;
+    const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = i % Mv;
+        const size_t blk = i / Mv;
+        const int comp = (int)(blk % D);
+        const size_t j = blk / D;
+        int c[3];
+        coords<D>(s, g, c);
+        const float xi = x[i];
+        float lap = 0.0f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            float t = 0.0f;
+            if (c[a] > 0) t += xi - x[i - stride[a]];
+            if (c[a] < g.m[a] - 1) t += xi - x[i + stride[a]];
+            lap = fmaf(t, g.inv_h[a] * g.inv_h[a], lap);
+        }
+        // transpose of the centred difference along axis comp
+        const float* dj = div + j * Mv;
+        const int ci = c[comp], m = g.m[comp];
+        const size_t st = stride[comp];
+        float dt = 0.0f;
+        if (ci >= 1) dt += dj[s - st];
+        if (ci == m - 1) dt += dj[s];
+        if (ci + 1 <= m - 1) dt -= dj[s + st];
+        if (ci == 0) dt -= dj[s];
+        dt *= 0.5f * g.inv_h[comp];
+        float r = smu * lap + slm * dt + gamma * xi;
+        if (addsrc != nullptr) r += addsrc[i];
+        out[i] = r;
+    }
+}
+
+// ------------------------------------------------------------------ DCT --
+
+// out[.., k, ..] = sum_i C[k][i] in[.., i, ..] along one axis (inverse: C[i][k]);
+// C is the orthonormal DCT-II matrix of that axis.
+__global__ void dct_axis_kernel(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ C,
+                                DevGrid g, int nblk, int axis, int inverse) {
+    const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t total = Mv * nblk;
+    const int m = g.m[axis];
+    const size_t st = (axis == 0) ? 1 : (axis == 1 ? (size_t)g.m[0] : (size_t)g.m[0] * g.m[1]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = i % Mv;
+        const int k = (int)((s / st) % m);
+        const size_t base = i - (size_t)k * st;
+        float acc = 0.0f;
+        if (inverse) {
+            for (int q = 0; q < m; ++q) acc = fmaf(__ldg(C + (size_t)q * m + k), in[base + q * st], acc);
+        } else {
+            const float* row = C + (size_t)k * m;
+            for (int q = 0; q < m; ++q) acc = fmaf(__ldg(row + q), in[base + q * st], acc);
+        }
+        out[i] = acc;
+    }
+}
+
+__global__ void scale_modes_kernel(float* x, const float* __restrict__ inv_eig, size_t block_elems, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        x[i] *= inv_eig[i % block_elems];
+}
+
+__global__ void axpby_kernel(float a, const float* __restrict__ x, float b, float* y, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = fmaf(a, x[i], b * y[i]);
+}
+
+__global__ void add_scaled_kernel(float* out, const float* x, float ax, const float* y, float ay, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = fmaf(ax, x[i], ay * y[i]);
+}
+
+inline int grid_for(size_t count) {
+    const size_t b = (count + kBlock - 1) / kBlock;
+    return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, cudaStream_t s) {
+    const size_t total = (size_t)g.mp[0] * g.mp[1] * g.mp[2] * K;
+    if (d == 3) pack_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, K);
+    else pack_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_velocity(int d, const void* Gp, float* out, const DevGrid& g, int K, float scale,
+                                   cudaStream_t s) {
+    const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * K;
+    if (d == 3) unpack_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>((const float*)Gp, out, g, K, scale);
+    else unpack_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>((const float*)Gp, out, g, K, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_image(const float* T, float* Tp, const DevGrid& g, int d, float scale, cudaStream_t s) {
+    const size_t total = (size_t)g.mp[0] * g.mp[1] * g.mp[2];
+    pack_image_kernel<<<grid_for(total), kBlock, 0, s>>>(T, Tp, g, d, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_image(const float* acc, float* out, const DevGrid& g, int d, cudaStream_t s) {
+    const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
+    unpack_image_kernel<<<grid_for(M), kBlock, 0, s>>>(acc, out, g, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repad_image(float* acc, const DevGrid& g, int d, float scale, cudaStream_t s) {
+    const size_t total = (size_t)g.mp[0] * g.mp[1] * g.mp[2];
+    repad_image_kernel<<<grid_for(total), kBlock, 0, s>>>(acc, g, d, scale);
+    return cudaGetLastError();
+}
+
+int residual_blocks(const DevGrid& g, int d) {
+    (void)d;
+    const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const int b = nblocks_for(M);
+    return b < kReduceBlocks ? b : kReduceBlocks;
+}
+
+cudaError_t launch_residual(const float* u1, const float* R, float* rp, const DevGrid& g, int d, float scale,
+                            double* partial, int nblocks, cudaStream_t s) {
+    residual_kernel<<<nblocks, kBlock, 0, s>>>(u1, R, rp, g, d, scale, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double* partial, int count, double* out, cudaStream_t s) {
+    reduce_kernel<<<1, kBlock, 0, s>>>(partial, count, out);
+    return cudaGetLastError();
+}
+
+int dot_blocks(size_t count) {
+    const int b = nblocks_for(count);
+    return b < kReduceBlocks ? (b > 0 ? b : 1) : kReduceBlocks;
+}
+
+cudaError_t launch_dot(const float* a, const float* b, size_t count, double* partial, int nblocks, cudaStream_t s) {
+    dot_kernel<<<nblocks, kBlock, 0, s>>>(a, b, count, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_laplacian(int d, const float* x, float* out, const DevGrid& g, int blocks_kd, float scale,
+                             float gamma, const float* addsrc, cudaStream_t s) {
+    const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * blocks_kd;
+    const float* gsrc = gamma != 0.0f ? x : nullptr;
+    if (d == 3) laplacian_kernel<3><<<grid_for(total), kBlock, 0, s>>>(x, out, g, blocks_kd, scale, gamma, gsrc, addsrc);
+    else laplacian_kernel<2><<<grid_for(total), kBlock, 0, s>>>(x, out, g, blocks_kd, scale, gamma, gsrc, addsrc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_laplacian_ext(int d, const float* x, float* out, const DevGrid& g, int blocks_kd, float scale,
+                                 float gamma, const float* gsrc, const float* addsrc, cudaStream_t s) {
+    const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * blocks_kd;
+    if (d == 3) laplacian_kernel<3><<<grid_for(total), kBlock, 0, s>>>(x, out, g, blocks_kd, scale, gamma, gsrc, addsrc);
+    else laplacian_kernel<2><<<grid_for(total), kBlock, 0, s>>>(x, out, g, blocks_kd, scale, gamma, gsrc, addsrc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divergence(int d, const float* x, float* div, const DevGrid& g, int K, cudaStream_t s) {
+    const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * K;
+    if (d == 3) divergence_kernel<3><<<grid_for(total), kBlock, 0, s>>>(x, div, g, K);
+    else divergence_kernel<2><<<grid_for(total), kBlock, 0, s>>>(x, div, g, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_elastic(int d, const float* x, const float* div, float* out, const DevGrid& g, int K,
+                           float smu, float slm, float gamma, const float* addsrc, cudaStream_t s) {
+    const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * K * d;
+    if (d == 3) elastic_kernel<3><<<grid_for(total), kBlock, 0, s>>>(x, div, out, g, K, smu, slm, gamma, addsrc);
+    else elastic_kernel<2><<<grid_for(total), kBlock, 0, s>>>(x, div, out, g, K, smu, slm, gamma, addsrc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const DevGrid& g, int d, int nblocks_kd,
+                            int axis, bool inverse, cudaStream_t s) {
+    (void)d;
+    const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * nblocks_kd;
+    dct_axis_kernel<<<grid_for(total), kBlock, 0, s>>>(in, out, C, g, nblocks_kd, axis, inverse ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_modes(float* x, const float* inv_eig, size_t block_elems, size_t count, cudaStream_t s) {
+    scale_modes_kernel<<<grid_for(count), kBlock, 0, s>>>(x, inv_eig, block_elems, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(float a, const float* x, float b, float* y, size_t count, cudaStream_t s) {
+    axpby_kernel<<<grid_for(count), kBlock, 0, s>>>(a, x, b, y, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_scaled(float* out, const float* x, float ax, const float* y, float ay, size_t count,
+                              cudaStream_t s) {
+    add_scaled_kernel<<<grid_for(count), kBlock, 0, s>>>(out, x, ax, y, ay, count);
+    return cudaGetLastError();
+}

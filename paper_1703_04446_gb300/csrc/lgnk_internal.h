@@ -1,0 +1,86 @@
+// Internal declarations of the lgnk CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lgnk.h"
+
+// Grid data is stored padded by LGNK_PAD zero nodes on each side of every axis.
+// A point's lower cell corner is clamped to [-2, m], so both corners of any
+// point, however far outside, fall on padded storage; padding holds zeros for
+// gathers (zero extension) and swallows scatters that the unpack then drops
+// (the adjoint of zero extension: splatted mass that leaves the grid is lost).
+#define LGNK_PAD 2
+#define LGNK_MAX_STEPS 64
+#define LGNK_BLOCK 256
+
+struct DevGrid {
+    int m[3];      // cells per axis (1 for an absent axis)
+    int mp[3];     // padded extents m + 2 * LGNK_PAD (1 for an absent axis)
+    float lo[3];   // domain lower corner
+    float h[3];    // cell widths
+    float inv_h[3];
+};
+
+enum TraceMode { MODE_FWD = 0, MODE_JVP = 1, MODE_JTVP = 2, MODE_HESS = 3, MODE_OBJGRAD = 4 };
+
+// Arguments of one launch of the characteristic-tracing kernel family.
+struct TraceArgs {
+    DevGrid ig, vg;
+    int K, N;
+    float dt, t0;
+    float cellvol;            // image cell volume h^d (SSD weight)
+    int tiles[3];             // voxel tiles per axis (grid = product)
+    const void* V;            // packed velocity, [zp][yp][xp][K] of float4 (3D) / float2 (2D)
+    const void* dV;           // packed direction (JVP, HESS)
+    const float* Tp;          // padded template (gathers)
+    const float* T;           // template, ABI layout (continuity particle masses)
+    const float* R;           // reference, ABI layout (OBJGRAD, FWD with residual)
+    const float* r;           // JTVP seed: transport ABI layout r; continuity padded r
+    float* u1;                // transport FWD output (ABI layout)
+    float* yout;              // optional end points [d][M]
+    float* acc;               // continuity splat accumulator (padded image)
+    void* G;                  // packed gradient accumulator (JTVP, HESS, OBJGRAD)
+    double* partial;          // per-block FP64 partial sums of res^2
+};
+
+// trace kernels (trace2d.cu / trace3d.cu)
+cudaError_t launch_trace(int d, bool nonstat, int model, int mode, const TraceArgs& a, int nblocks,
+                         cudaStream_t s);
+
+// grid utilities (grid_ops.cu)
+cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, cudaStream_t s);
+cudaError_t launch_unpack_velocity(int d, const void* Gp, float* out, const DevGrid& g, int K,
+                                   float scale, cudaStream_t s);
+cudaError_t launch_pack_image(const float* T, float* Tp, const DevGrid& g, int d, float scale, cudaStream_t s);
+cudaError_t launch_unpack_image(const float* acc, float* out, const DevGrid& g, int d, cudaStream_t s);
+cudaError_t launch_repad_image(float* acc, const DevGrid& g, int d, float scale, cudaStream_t s);
+cudaError_t launch_residual(const float* u1, const float* R, float* rp, const DevGrid& g, int d,
+                            float scale, double* partial, int nblocks, cudaStream_t s);
+int residual_blocks(const DevGrid& g, int d);
+cudaError_t launch_reduce(const double* partial, int count, double* out, cudaStream_t s);
+cudaError_t launch_dot(const float* a, const float* b, size_t count, double* partial, int nblocks,
+                       cudaStream_t s);
+int dot_blocks(size_t count);
+// out = addsrc + scale * A x + gamma * x for the Neumann Laplacian A = B^T B of each
+// (time node, component) block; addsrc may be NULL or equal to out.
+cudaError_t launch_laplacian(int d, const float* x, float* out, const DevGrid& g, int blocks_kd,
+                             float scale, float gamma, const float* addsrc, cudaStream_t s);
+// as above with the gamma term taken from gsrc instead of x
+cudaError_t launch_laplacian_ext(int d, const float* x, float* out, const DevGrid& g, int blocks_kd,
+                                 float scale, float gamma, const float* gsrc, const float* addsrc,
+                                 cudaStream_t s);
+cudaError_t launch_divergence(int d, const float* x, float* div, const DevGrid& g, int K, cudaStream_t s);
+// out_c = addsrc + smu * A x_c + slm * D_c^T div + gamma * x_c (elastic operator)
+cudaError_t launch_elastic(int d, const float* x, const float* div, float* out, const DevGrid& g, int K,
+                           float smu, float slm, float gamma, const float* addsrc, cudaStream_t s);
+cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const DevGrid& g, int d,
+                            int nblocks_kd, int axis, bool inverse, cudaStream_t s);
+cudaError_t launch_scale_modes(float* x, const float* inv_eig, size_t block_elems, size_t count,
+                               cudaStream_t s);
+// y = a * x + b * y  (count floats)
+cudaError_t launch_axpby(float a, const float* x, float b, float* y, size_t count, cudaStream_t s);
+cudaError_t launch_add_scaled(float* out, const float* x, float ax, const float* y, float ay, size_t count,
+                              cudaStream_t s);

@@ -1,0 +1,7 @@
+// 2D instantiations of the characteristic-tracing kernel family.
+#include "trace_impl.cuh"
+
+cudaError_t launch_trace_2d(bool nonstat, int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s) {
+    return nonstat ? lgnk::launch_dim<2, true>(model, mode, a, nblocks, s)
+                   : lgnk::launch_dim<2, false>(model, mode, a, nblocks, s);
+}

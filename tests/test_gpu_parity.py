@@ -1,0 +1,198 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by
+element on seeded inputs that span several tiles and ragged tails.
+
+Tolerances (FP32 tracing against FP64): forward state and J / J^T / H
+products <= 1e-5 relative L2; objective <= 1e-5 relative (the bar for the
+final objective is 1e-4)."""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lagrangian as L
+from oracle.objective import gradient, hessvec, objective, reg_operator
+from oracle.solver import apply_preconditioner
+from tests._cases import CASES, make_case, rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(name):
+    op, gp, a = make_case(name)
+    f64 = {k: v.astype(np.float64) for k, v in a.items()}
+    u1, y = L.final_state(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N)
+    out = dict(u1=u1, y=y,
+               jvp=L.jvp(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N, f64["dv"]),
+               jtvp=L.jtvp(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N, f64["r"]),
+               hess=hessvec(op, f64["v"], f64["T"], f64["dv"]),
+               obj=objective(op, f64["v"], f64["T"], f64["R"])[:3],
+               grad=gradient(op, f64["v"], f64["T"], f64["R"]),
+               prec=apply_preconditioner(op, f64["dv"]))
+    return out
+
+
+@functools.lru_cache(maxsize=None)
+def _gpu(name):
+    from paper_1703_04446_gb300 import lgnk
+    op, gp, a = make_case(name)
+    ctx = lgnk.Context(lgnk.Problem(**gp))
+    t = {k: torch.from_numpy(v).cuda() for k, v in a.items()}
+    return ctx, t
+
+
+def _np(x):
+    return x.detach().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forward_state(name):
+    ctx, t = _gpu(name)
+    u1, y = ctx.forward(t["v"], t["T"], return_y=True)
+    o = _oracle(name)
+    assert rel(_np(u1), o["u1"]) <= TOL
+    assert rel(_np(y).reshape(len(ctx.problem.image_m), -1), o["y"]) <= 1e-6
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_jvp(name):
+    ctx, t = _gpu(name)
+    assert rel(_np(ctx.jvp(t["v"], t["T"], t["dv"])), _oracle(name)["jvp"]) <= TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_jtvp(name):
+    ctx, t = _gpu(name)
+    assert rel(_np(ctx.jtvp(t["v"], t["T"], t["r"])), _oracle(name)["jtvp"]) <= TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hessvec(name):
+    ctx, t = _gpu(name)
+    assert rel(_np(ctx.hessvec(t["v"], t["T"], t["dv"])), _oracle(name)["hess"]) <= TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_objective_and_gradient(name):
+    ctx, t = _gpu(name)
+    J, D, S, g = ctx.objective(t["v"], t["T"], t["R"], grad=True)
+    Jo, Do, So = _oracle(name)["obj"]
+    assert abs(J - Jo) <= TOL * abs(Jo)
+    assert abs(D - Do) <= TOL * abs(Do)
+    assert abs(S - So) <= TOL * abs(So)
+    assert rel(_np(g), _oracle(name)["grad"]) <= TOL
+    J2, D2, S2 = ctx.objective(t["v"], t["T"], t["R"])
+    assert abs(J2 - J) <= 1e-12 * abs(J)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_preconditioner(name):
+    ctx, t = _gpu(name)
+    assert rel(_np(ctx.precond(t["dv"])), _oracle(name)["prec"]) <= TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_identity_on_gpu(name):
+    """<J dv, r> = <dv, J^T r> within FP32 accumulation error."""
+    ctx, t = _gpu(name)
+    lhs = float(torch.sum(ctx.jvp(t["v"], t["T"], t["dv"]).double() * t["r"].double()))
+    rhs = float(torch.sum(ctx.jtvp(t["v"], t["T"], t["r"]).double() * t["dv"].double()))
+    assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs))
+
+
+def test_dot_is_fp64():
+    ctx, t = _gpu("2d_transport_64")
+    a = torch.full((1 << 20,), 1.0 + 2.0 ** -20, device="cuda")
+    b = torch.full((1 << 20,), 3.0, device="cuda")
+    assert ctx.dot(a, b) == pytest.approx(3.0 * (1.0 + 2.0 ** -20) * (1 << 20), rel=1e-15)
+
+
+def test_zero_velocity_is_identity():
+    for name in ("2d_transport_64", "3d_continuity_K2"):
+        ctx, t = _gpu(name)
+        u1 = ctx.forward(torch.zeros_like(t["v"]), t["T"])
+        np.testing.assert_allclose(_np(u1), t["T"].cpu().numpy(), rtol=0, atol=1e-6 * float(t["T"].abs().max()))
+
+
+def test_continuity_conserves_mass_on_gpu():
+    ctx, t = _gpu("2d_continuity_K5")
+    T = t["T"].clone()
+    T[:6] = 0
+    T[-6:] = 0
+    T[:, :6] = 0
+    T[:, -6:] = 0
+    u1 = ctx.forward(t["v"], T)
+    assert abs(float(u1.double().sum()) - float(T.double().sum())) <= 1e-6 * float(T.double().sum())
+
+
+def test_particles_leaving_the_domain_match_oracle():
+    """Large velocities push characteristics outside the grid: zero extension on
+    gathers, dropped mass on splats, exactly as the oracle."""
+    from paper_1703_04446_gb300 import lgnk
+    for model in ("transport", "continuity"):
+        op, gp, a = make_case("2d_transport_64")
+        op.model = gp["model"] = model
+        v = a["v"] * 6.0
+        ctx = lgnk.Context(lgnk.Problem(**gp))
+        u1 = ctx.forward(torch.from_numpy(v).cuda(), torch.from_numpy(a["T"]).cuda())
+        ref, y = L.final_state(model, v.astype(np.float64), op.vgrid, a["T"].astype(np.float64), op.igrid, op.N)
+        assert np.abs(y).max() > 1.1 or y.min() < -0.1
+        assert rel(_np(u1), ref) <= TOL
+
+
+def test_max_steps_and_degenerate_axis():
+    from paper_1703_04446_gb300 import lgnk
+    op, gp, a = make_case("2d_transport_64")
+    op.N = gp["rk4_steps"] = 64
+    ctx = lgnk.Context(lgnk.Problem(**gp))
+    tv, tT, tdv = (torch.from_numpy(a[k]).cuda() for k in ("v", "T", "dv"))
+    H = ctx.hessvec(tv, tT, tdv)
+    ref = hessvec(op, a["v"].astype(np.float64), a["T"].astype(np.float64), a["dv"].astype(np.float64))
+    assert rel(_np(H), ref) <= TOL
+    # a grid one cell thick along y
+    gp2 = dict(gp, image_m=(24, 1), velocity_m=(12, 1), rk4_steps=3)
+    from oracle.objective import Problem as OP
+    op2 = OP(L.Grid((24, 1)), L.Grid((12, 1)), K=1, N=3, alpha=op.alpha, gamma=op.gamma)
+    rng = np.random.default_rng(3)
+    T = rng.uniform(size=(1, 24)).astype(np.float32)
+    v = (0.02 * rng.normal(size=(1, 2, 1, 12))).astype(np.float32)
+    dv = (0.02 * rng.normal(size=(1, 2, 1, 12))).astype(np.float32)
+    ctx2 = lgnk.Context(lgnk.Problem(**gp2))
+    u1 = ctx2.forward(torch.from_numpy(v).cuda(), torch.from_numpy(T).cuda())
+    assert rel(_np(u1), L.final_state("transport", v.astype(np.float64), op2.vgrid, T.astype(np.float64),
+                                      op2.igrid, 3)[0]) <= TOL
+    H2 = ctx2.hessvec(torch.from_numpy(v).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(dv).cuda())
+    assert rel(_np(H2), hessvec(op2, v.astype(np.float64), T.astype(np.float64), dv.astype(np.float64))) <= TOL
+
+
+def test_aliasing_and_shape_errors():
+    from paper_1703_04446_gb300 import lgnk
+    ctx, t = _gpu("2d_transport_64")
+    with pytest.raises(lgnk.LgnkError):
+        ctx.hessvec(t["v"], t["T"], t["dv"], out=t["dv"])
+    with pytest.raises(ValueError):
+        ctx.forward(t["v"][..., :-1].contiguous(), t["T"])
+    with pytest.raises(ValueError):
+        ctx.forward(t["v"].double(), t["T"])
+
+
+def test_memory_budget_is_enforced():
+    from paper_1703_04446_gb300 import lgnk
+    op, gp, a = make_case("3d_transport_ragged")
+    with pytest.raises(lgnk.LgnkError) as e:
+        lgnk.Context(lgnk.Problem(**gp), mem_budget=1024)
+    assert e.value.status == 2
+    ctx = lgnk.Context(lgnk.Problem(**gp))
+    assert ctx.scratch_bytes > 0
+
+
+def test_regularizer_operator_through_hessvec_at_zero_image():
+    """With T = 0 the data term vanishes and H dv = alpha dt h^d A dv + gamma dv."""
+    for name in ("2d_transport_ragged_K3", "2d_continuity_K5", "3d_continuity_K2"):
+        op, gp, a = make_case(name)
+        ctx, t = _gpu(name)
+        H = ctx.hessvec(t["v"], torch.zeros_like(t["T"]), t["dv"])
+        ref = op.alpha * reg_operator(op, a["dv"].astype(np.float64)) + op.gamma * a["dv"].astype(np.float64)
+        assert rel(_np(H), ref) <= TOL
