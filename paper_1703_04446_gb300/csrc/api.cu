@@ -172,6 +172,18 @@ TraceArgs base_args(const lgnk_ctx* ctx) {
     a.t0 = transport ? 1.0f : 0.0f;
     a.cellvol = (float)ctx->cellvol;
     for (int i = 0; i < 3; ++i) a.tiles[i] = ctx->tiles[i];
+    for (int i = 0; i < 3; ++i) {
+        if (i < ctx->d) {
+            const lgnk_grid& gi = ctx->prob.image;
+            const lgnk_grid& gv = ctx->prob.velocity;
+            const double hi = (gi.hi[i] - gi.lo[i]) / gi.m[i], hv = (gv.hi[i] - gv.lo[i]) / gv.m[i];
+            a.vxi_a[i] = (gi.lo[i] - gv.lo[i]) / hv - 0.5;
+            a.vxi_b[i] = hi / hv;
+        } else {
+            a.vxi_a[i] = 0.0;
+            a.vxi_b[i] = 0.0;
+        }
+    }
     a.V = ctx->Vp;
     a.dV = ctx->dVp;
     a.Tp = ctx->Tp;

@@ -33,6 +33,9 @@ struct TraceArgs {
     float dt, t0;
     float cellvol;            // image cell volume h^d (SSD weight)
     int tiles[3];             // voxel tiles per axis (grid = product)
+    // continuous velocity-grid index of the start point of voxel i along axis a:
+    // vxi_a[a] + (i + 1/2) * vxi_b[a]  (exact in FP64: (x_c - lo_v) / h_v - 1/2)
+    double vxi_a[3], vxi_b[3];
     const void* V;            // packed velocity, [zp][yp][xp][K] of float4 (3D) / float2 (2D)
     const void* dV;           // packed direction (JVP, HESS)
     const float* Tp;          // padded template (gathers)

@@ -14,6 +14,15 @@
 //            voxel (u1 at voxel i depends only on characteristic i, so the
 //            JVP value feeds that voxel's JTVP seed directly).
 //   OBJGRAD  transport only: u1, SSD partials and the JTVP of h^d res fused.
+//
+// Position representation.  A characteristic starts at a cell centre x_c and
+// its state is the FP32 displacement u = y - x_c.  Looking a point up on a grid
+// uses the start's continuous grid index split into an integer I0 and a
+// fraction F0 (computed once in FP64): the cell is I0 + floor(F0 + u / h).  A
+// characteristic that barely moves off a grid node therefore keeps the sign of
+// its displacement (an absolute FP32 coordinate would round it away), and the
+// cell choice at the kinks of the piecewise-linear interpolant agrees with an
+// exact evaluation.
 #pragma once
 
 #include "lgnk_internal.h"
@@ -39,19 +48,53 @@ __device__ __forceinline__ void red_vec(float4* p, const float* x, float w) {
     atomicAdd(p, make_float4(w * x[0], w * x[1], w * x[2], 0.0f));
 }
 
-// Cell of point p on the padded grid: returns the padded linear index of the
-// lower corner and the fractional offsets f in [0, 1).  The continuous index is
-// clamped to [-2, m + 1/2] first, so any point (also NaN) maps to storage.
+// Start of one characteristic on one grid: continuous index I0 + F0 and the
+// clamp bounds of the offset t = F0 + u / h that keep I0 + floor(t) in [-2, m].
 template <int D>
-__device__ __forceinline__ int locate(const DevGrid& g, const float* p, float* f) {
-    int idx[3];
+struct Start {
+    int I0[D];
+    float F0[D];
+    float lo[D], hi[D];
+};
+
+template <int D>
+__device__ __forceinline__ void start_on_image(const DevGrid& g, const int* idx, Start<D>& s) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        float xi = fmaf(p[a] - g.lo[a], g.inv_h[a], -0.5f);
-        xi = fminf(fmaxf(xi, -2.0f), (float)g.m[a] + 0.5f);
-        const float fl = floorf(xi);
-        f[a] = xi - fl;
-        idx[a] = (int)fl + LGNK_PAD;
+        s.I0[a] = idx[a];
+        s.F0[a] = 0.0f;
+        s.lo[a] = (float)(-2 - idx[a]);
+        s.hi[a] = (float)(g.m[a] - idx[a]) + 0.5f;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void start_on_velocity(const TraceArgs& A, const int* idx, Start<D>& s) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double xi = A.vxi_a[a] + ((double)idx[a] + 0.5) * A.vxi_b[a];
+        const double fl = floor(xi);
+        const int i0 = (int)fmax(fmin(fl, (double)A.vg.m[a]), -2.0);
+        s.I0[a] = i0;
+        s.F0[a] = (float)(xi - (double)i0);
+        s.lo[a] = (float)(-2 - i0);
+        s.hi[a] = (float)(A.vg.m[a] - i0) + 0.5f;
+    }
+}
+
+// Cell of the point at displacement u from the start: padded linear index of the
+// lower corner and fractional offsets f in [0, 1].  NaN maps to the lowest
+// clamp, so any point addresses padded storage.
+template <int D>
+__device__ __forceinline__ int locate(const DevGrid& g, const Start<D>& s, const float* u, float* f) {
+    int idx[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        float t = fmaf(u[a], g.inv_h[a], s.F0[a]);
+        t = fminf(fmaxf(t, s.lo[a]), s.hi[a]);
+        const float fl = floorf(t);
+        f[a] = t - fl;
+        idx[a] = s.I0[a] + (int)fl + LGNK_PAD;
     }
     if (D == 3) return idx[0] + g.mp[0] * (idx[1] + g.mp[1] * idx[2]);
     return idx[0] + g.mp[0] * idx[1];
@@ -165,12 +208,12 @@ __device__ __forceinline__ void scatter_velocity(const DevGrid& g, int K, typena
     }
 }
 
-// T(p) and optionally grad T(p) from the padded image.
+// T(y) and optionally grad T(y) from the padded image, y at displacement u.
 template <int D, bool GRAD>
-__device__ __forceinline__ float sample_image(const DevGrid& g, const float* __restrict__ Tp, const float* p,
-                                              float* grad) {
+__device__ __forceinline__ float sample_image(const DevGrid& g, const Start<D>& s, const float* __restrict__ Tp,
+                                              const float* u, float* grad) {
     float f[D];
-    const int base = locate<D>(g, p, f);
+    const int base = locate<D>(g, s, u, f);
     float val = 0.0f;
     if (GRAD) {
 #pragma unroll
@@ -190,12 +233,12 @@ __device__ __forceinline__ float sample_image(const DevGrid& g, const float* __r
     return val;
 }
 
-// acc += mass * w(p) (push-forward, Eq. 7) or mass * (grad_y w(p) . dp).
+// acc += mass * w(y) (push-forward, Eq. 7) or mass * (grad_y w(y) . dp).
 template <int D, bool TANGENT>
-__device__ __forceinline__ void splat_image(const DevGrid& g, float* acc, const float* p, float mass,
-                                            const float* dp) {
+__device__ __forceinline__ void splat_image(const DevGrid& g, const Start<D>& s, float* acc, const float* u,
+                                            float mass, const float* dp) {
     float f[D];
-    const int base = locate<D>(g, p, f);
+    const int base = locate<D>(g, s, u, f);
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
         float dw[D];
@@ -213,34 +256,35 @@ __device__ __forceinline__ void splat_image(const DevGrid& g, float* acc, const 
     }
 }
 
-// One RK4 step of the characteristic (Alg. 1 without the derivative).
+// One RK4 step of the characteristic (Alg. 1 without the derivative), on the
+// displacement u.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_step(const TraceArgs& A, const typename VecT<D>::type* V, float* y,
-                                         float tk) {
+__device__ __forceinline__ void rk4_step(const TraceArgs& A, const Start<D>& sv,
+                                         const typename VecT<D>::type* V, float* u, float tk) {
     int j1, j2, j4;
     float th1, th2, th4;
     time_slot(A.K, tk, j1, th1);
     time_slot(A.K, tk + 0.5f * A.dt, j2, th2);
     time_slot(A.K, tk + A.dt, j4, th4);
     const float dt = A.dt, hdt = 0.5f * A.dt;
-    float f[D], v1[D], v2[D], v3[D], v4[D], ys[D];
-    int b = locate<D>(A.vg, y, f);
+    float f[D], v1[D], v2[D], v3[D], v4[D], us[D];
+    int b = locate<D>(A.vg, sv, u, f);
     sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j1, th1, v1, nullptr, nullptr);
 #pragma unroll
-    for (int a = 0; a < D; ++a) ys[a] = fmaf(hdt, v1[a], y[a]);
-    b = locate<D>(A.vg, ys, f);
+    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, v1[a], u[a]);
+    b = locate<D>(A.vg, sv, us, f);
     sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j2, th2, v2, nullptr, nullptr);
 #pragma unroll
-    for (int a = 0; a < D; ++a) ys[a] = fmaf(hdt, v2[a], y[a]);
-    b = locate<D>(A.vg, ys, f);
+    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, v2[a], u[a]);
+    b = locate<D>(A.vg, sv, us, f);
     sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j2, th2, v3, nullptr, nullptr);
 #pragma unroll
-    for (int a = 0; a < D; ++a) ys[a] = fmaf(dt, v3[a], y[a]);
-    b = locate<D>(A.vg, ys, f);
+    for (int a = 0; a < D; ++a) us[a] = fmaf(dt, v3[a], u[a]);
+    b = locate<D>(A.vg, sv, us, f);
     sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j4, th4, v4, nullptr, nullptr);
     const float s6 = dt / 6.0f;
 #pragma unroll
-    for (int a = 0; a < D; ++a) y[a] = fmaf(s6, v1[a] + 2.0f * (v2[a] + v3[a]) + v4[a], y[a]);
+    for (int a = 0; a < D; ++a) u[a] = fmaf(s6, v1[a] + 2.0f * (v2[a] + v3[a]) + v4[a], u[a]);
 }
 
 template <int D>
@@ -268,8 +312,9 @@ __device__ __forceinline__ void rmatvec(const float* J, const float* x, float* o
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const typename VecT<D>::type* V,
-                                                 const typename VecT<D>::type* dV, float* y, float* dy,
+__device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const Start<D>& sv,
+                                                 const typename VecT<D>::type* V,
+                                                 const typename VecT<D>::type* dV, float* u, float* dy,
                                                  float tk) {
     int j1, j2, j4;
     float th1, th2, th4;
@@ -277,37 +322,37 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const typen
     time_slot(A.K, tk + 0.5f * A.dt, j2, th2);
     time_slot(A.K, tk + A.dt, j4, th4);
     const float dt = A.dt, hdt = 0.5f * A.dt;
-    float f[D], ys[D], q[D], J[D * D], dvs[D], Jq[D];
+    float f[D], us[D], q[D], J[D * D], dvs[D], Jq[D];
     float v1[D], v2[D], v3[D], v4[D], D1[D], D2[D], D3[D], D4[D];
 
-    int b = locate<D>(A.vg, y, f);
+    int b = locate<D>(A.vg, sv, u, f);
     sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j1, th1, v1, J, dvs);
     matvec<D>(J, dy, Jq);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         D1[a] = dvs[a] + Jq[a];
-        ys[a] = fmaf(hdt, v1[a], y[a]);
+        us[a] = fmaf(hdt, v1[a], u[a]);
         q[a] = fmaf(hdt, D1[a], dy[a]);
     }
-    b = locate<D>(A.vg, ys, f);
+    b = locate<D>(A.vg, sv, us, f);
     sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j2, th2, v2, J, dvs);
     matvec<D>(J, q, Jq);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         D2[a] = dvs[a] + Jq[a];
-        ys[a] = fmaf(hdt, v2[a], y[a]);
+        us[a] = fmaf(hdt, v2[a], u[a]);
         q[a] = fmaf(hdt, D2[a], dy[a]);
     }
-    b = locate<D>(A.vg, ys, f);
+    b = locate<D>(A.vg, sv, us, f);
     sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j2, th2, v3, J, dvs);
     matvec<D>(J, q, Jq);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         D3[a] = dvs[a] + Jq[a];
-        ys[a] = fmaf(dt, v3[a], y[a]);
+        us[a] = fmaf(dt, v3[a], u[a]);
         q[a] = fmaf(dt, D3[a], dy[a]);
     }
-    b = locate<D>(A.vg, ys, f);
+    b = locate<D>(A.vg, sv, us, f);
     sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j4, th4, v4, J, dvs);
     matvec<D>(J, q, Jq);
     const float s6 = dt / 6.0f;
@@ -315,16 +360,16 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const typen
     for (int a = 0; a < D; ++a) {
         D4[a] = dvs[a] + Jq[a];
         dy[a] = fmaf(s6, D1[a] + 2.0f * (D2[a] + D3[a]) + D4[a], dy[a]);
-        y[a] = fmaf(s6, v1[a] + 2.0f * (v2[a] + v3[a]) + v4[a], y[a]);
+        u[a] = fmaf(s6, v1[a] + 2.0f * (v2[a] + v3[a]) + v4[a], u[a]);
     }
 }
 
 // Transpose of one tangent step: given lam (adjoint of the step's end point),
 // scatter the step's contribution into G and return the adjoint of its start.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const typename VecT<D>::type* V,
-                                                 typename VecT<D>::type* G, const float* y, float* lam,
-                                                 float tk) {
+__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const Start<D>& sv,
+                                                 const typename VecT<D>::type* V, typename VecT<D>::type* G,
+                                                 const float* u, float* lam, float tk) {
     int j1, j2, j4;
     float th1, th2, th4;
     time_slot(A.K, tk, j1, th1);
@@ -332,20 +377,20 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const typen
     time_slot(A.K, tk + A.dt, j4, th4);
     const float dt = A.dt, hdt = 0.5f * A.dt;
     float f1[D], f2[D], f3[D], f4[D], J1[D * D], J2[D * D], J3[D * D], J4[D * D];
-    float vs[D], ys[D];
-    const int b1 = locate<D>(A.vg, y, f1);
+    float vs[D], us[D];
+    const int b1 = locate<D>(A.vg, sv, u, f1);
     sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b1, f1, j1, th1, vs, J1, nullptr);
 #pragma unroll
-    for (int a = 0; a < D; ++a) ys[a] = fmaf(hdt, vs[a], y[a]);
-    const int b2 = locate<D>(A.vg, ys, f2);
+    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, vs[a], u[a]);
+    const int b2 = locate<D>(A.vg, sv, us, f2);
     sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b2, f2, j2, th2, vs, J2, nullptr);
 #pragma unroll
-    for (int a = 0; a < D; ++a) ys[a] = fmaf(hdt, vs[a], y[a]);
-    const int b3 = locate<D>(A.vg, ys, f3);
+    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, vs[a], u[a]);
+    const int b3 = locate<D>(A.vg, sv, us, f3);
     sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b3, f3, j2, th2, vs, J3, nullptr);
 #pragma unroll
-    for (int a = 0; a < D; ++a) ys[a] = fmaf(dt, vs[a], y[a]);
-    const int b4 = locate<D>(A.vg, ys, f4);
+    for (int a = 0; a < D; ++a) us[a] = fmaf(dt, vs[a], u[a]);
+    const int b4 = locate<D>(A.vg, sv, us, f4);
     sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b4, f4, j4, th4, vs, J4, nullptr);
 
     float mu[D], nu[D], acc[D];
@@ -405,60 +450,67 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
     const int by = b % A.tiles[1];
     const int bz = b / A.tiles[1];
     const int t = threadIdx.x;
-    const int ix = bx * Tile<D>::X + t % Tile<D>::X;
-    const int iy = by * Tile<D>::Y + (t / Tile<D>::X) % Tile<D>::Y;
-    const int iz = bz * Tile<D>::Z + t / (Tile<D>::X * Tile<D>::Y);
-    const bool active = ix < A.ig.m[0] && iy < A.ig.m[1] && (D == 2 || iz < A.ig.m[2]);
+    int idx[3];
+    idx[0] = bx * Tile<D>::X + t % Tile<D>::X;
+    idx[1] = by * Tile<D>::Y + (t / Tile<D>::X) % Tile<D>::Y;
+    idx[2] = bz * Tile<D>::Z + t / (Tile<D>::X * Tile<D>::Y);
+    const bool active = idx[0] < A.ig.m[0] && idx[1] < A.ig.m[1] && (D == 2 || idx[2] < A.ig.m[2]);
     double ssd = 0.0;
 
     if (active) {
-        const int vox = ix + A.ig.m[0] * (iy + A.ig.m[1] * iz);
-        float y[D], dy[D];
-        y[0] = A.ig.lo[0] + ((float)ix + 0.5f) * A.ig.h[0];
-        y[1] = A.ig.lo[1] + ((float)iy + 0.5f) * A.ig.h[1];
-        if (D == 3) y[D - 1] = A.ig.lo[D - 1] + ((float)iz + 0.5f) * A.ig.h[D - 1];
+        const int vox = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
+        Start<D> si, sv;
+        start_on_image<D>(A.ig, idx, si);
+        start_on_velocity<D>(A, idx, sv);
+        float u[D], dy[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) dy[a] = 0.0f;
+        for (int a = 0; a < D; ++a) {
+            u[a] = 0.0f;
+            dy[a] = 0.0f;
+        }
         float hist[ADJOINT ? LGNK_MAX_STEPS : 1][D];
 
         for (int k = 0; k < A.N; ++k) {
             const float tk = A.t0 + (float)k * A.dt;
             if (ADJOINT) {
 #pragma unroll
-                for (int a = 0; a < D; ++a) hist[ADJOINT ? k : 0][a] = y[a];
+                for (int a = 0; a < D; ++a) hist[ADJOINT ? k : 0][a] = u[a];
             }
-            if (TANGENT) rk4_tangent_step<D, NS>(A, V, dV, y, dy, tk);
-            else rk4_step<D, NS>(A, V, y, tk);
+            if (TANGENT) rk4_tangent_step<D, NS>(A, sv, V, dV, u, dy, tk);
+            else rk4_step<D, NS>(A, sv, V, u, tk);
         }
         if (A.yout != nullptr) {
             const int M = A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
 #pragma unroll
-            for (int a = 0; a < D; ++a) A.yout[(size_t)a * M + vox] = y[a];
+            for (int a = 0; a < D; ++a) {
+                const float xc = A.ig.lo[a] + ((float)idx[a] + 0.5f) * A.ig.h[a];
+                A.yout[(size_t)a * M + vox] = xc + u[a];
+            }
         }
 
         float lam[D];
         if (MODEL == LGNK_TRANSPORT) {
             float gT[D];
             if (MODE == MODE_FWD) {
-                const float u = sample_image<D, false>(A.ig, A.Tp, y, nullptr);
-                A.u1[vox] = u;
+                const float val = sample_image<D, false>(A.ig, si, A.Tp, u, nullptr);
+                A.u1[vox] = val;
                 if (A.R != nullptr) {
-                    const double r = (double)u - (double)A.R[vox];
+                    const double r = (double)val - (double)A.R[vox];
                     ssd = r * r;
                 }
             } else if (MODE == MODE_JVP) {
-                sample_image<D, true>(A.ig, A.Tp, y, gT);
+                sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 float du = 0.0f;
 #pragma unroll
                 for (int a = 0; a < D; ++a) du = fmaf(gT[a], dy[a], du);
                 A.u1[vox] = du;
             } else if (MODE == MODE_JTVP) {
-                sample_image<D, true>(A.ig, A.Tp, y, gT);
+                sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 const float r = A.r[vox];
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = r * gT[a];
             } else if (MODE == MODE_HESS) {
-                sample_image<D, true>(A.ig, A.Tp, y, gT);
+                sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 float du = 0.0f;
 #pragma unroll
                 for (int a = 0; a < D; ++a) du = fmaf(gT[a], dy[a], du);
@@ -466,9 +518,9 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = s * gT[a];
             } else {  // MODE_OBJGRAD
-                const float u = sample_image<D, true>(A.ig, A.Tp, y, gT);
-                if (A.u1 != nullptr) A.u1[vox] = u;
-                const float r = u - A.R[vox];
+                const float val = sample_image<D, true>(A.ig, si, A.Tp, u, gT);
+                if (A.u1 != nullptr) A.u1[vox] = val;
+                const float r = val - A.R[vox];
                 ssd = (double)r * (double)r;
                 const float s = A.cellvol * r;
 #pragma unroll
@@ -477,12 +529,12 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
         } else {
             const float mass = __ldg(A.T + vox);
             if (MODE == MODE_FWD) {
-                splat_image<D, false>(A.ig, A.acc, y, mass, nullptr);
+                splat_image<D, false>(A.ig, si, A.acc, u, mass, nullptr);
             } else if (MODE == MODE_JVP) {
-                splat_image<D, true>(A.ig, A.acc, y, mass, dy);
+                splat_image<D, true>(A.ig, si, A.acc, u, mass, dy);
             } else if (MODE == MODE_JTVP) {
                 float gr[D];
-                sample_image<D, true>(A.ig, A.r, y, gr);
+                sample_image<D, true>(A.ig, si, A.r, u, gr);
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = mass * gr[a];
             }
@@ -491,7 +543,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
         if (ADJOINT) {
             for (int k = A.N - 1; k >= 0; --k) {
                 const float tk = A.t0 + (float)k * A.dt;
-                rk4_adjoint_step<D, NS>(A, V, G, hist[ADJOINT ? k : 0], lam, tk);
+                rk4_adjoint_step<D, NS>(A, sv, V, G, hist[ADJOINT ? k : 0], lam, tk);
             }
         }
     }
