@@ -72,21 +72,31 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            time.sleep(1.0)   # let nvidia-smi start before the timed region opens
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, start: bool):
+        """Open (start=True) or close the timed window; only samples inside it count."""
+        now = time.time()
+        if start:
+            self.window = [now, None]
+        elif self.window:
+            self.window[1] = now
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -99,7 +109,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo, hi = (self.window or [0.0, None])
+        hi = (hi or time.time()) + 0.06
+        for ts, ln in self.lines:
+            if not (lo <= ts <= hi):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -240,12 +254,14 @@ def run_gpu(args):
     ctx.profile(True)
     with ClockSampler(local) as clk:
         barrier()
+        clk.mark(True)
         for k in range(args.steps):
             flush.fill_(float(k))
             starts[k].record(stream)
             ctx.hessvec(tv, tT, tdv, out)
             ends[k].record(stream)
         barrier()
+        clk.mark(False)
     kern_ms, kern_n, launches = ctx.profile_read()
     ctx.profile(False)
     step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
@@ -337,7 +353,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lgnk", choices=["lgnk", "reference"])
     ap.add_argument("--max-gn", type=int, default=30)

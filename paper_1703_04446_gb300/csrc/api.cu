@@ -184,6 +184,22 @@ TraceArgs base_args(const lgnk_ctx* ctx) {
             a.vxi_b[i] = 0.0;
         }
     }
+    // shared-memory gradient tile of the adjoint kernels (stationary fields)
+    a.sm_bytes = 0;
+    if (ctx->K == 1) {
+        int ts[3];
+        trace_tile_shape(ctx->d, MODE_HESS, false, ts);
+        size_t nodes = 1;
+        for (int i = 0; i < 3; ++i) {
+            a.smE[i] = 1;
+            if (i < ctx->d) {
+                a.smE[i] = (int)std::floor((ts[i] - 1) * a.vxi_b[i]) + 3 + 2 * LGNK_HALO;
+                nodes *= (size_t)a.smE[i];
+            }
+        }
+        const size_t bytes = nodes * ctx->d * sizeof(float);
+        if (bytes <= LGNK_TILE_SMEM_MAX) a.sm_bytes = (int)bytes;
+    }
     a.V = ctx->Vp;
     a.dV = ctx->dVp;
     a.Tp = ctx->Tp;
@@ -199,6 +215,14 @@ lgnk_status record_event(lgnk_ctx* ctx) {
     }
     CK(cudaEventRecord(ctx->ev[ctx->ev_used++], ctx->stream));
     return LGNK_OK;
+}
+
+int trace_blocks_for(const lgnk_ctx* ctx, int mode) {
+    int ts[3];
+    trace_tile_shape(ctx->d, mode, ctx->K > 1, ts);
+    int n = 1;
+    for (int i = 0; i < 3; ++i) n *= (ctx->ig.m[i] + ts[i] - 1) / ts[i];
+    return n;
 }
 
 lgnk_status trace(lgnk_ctx* ctx, int mode, const TraceArgs& a) {
@@ -302,7 +326,7 @@ lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, cons
     TraceArgs a = base_args(ctx);
     a.R = R;
     a.partial = ctx->partial;
-    int nred = ctx->trace_blocks;
+    int nred = trace_blocks_for(ctx, grad != nullptr ? MODE_OBJGRAD : MODE_FWD);
     if (ctx->prob.model == LGNK_TRANSPORT) {
         if (grad != nullptr) {
             TRY(zero_G(ctx));
@@ -477,11 +501,12 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     ctx->ipad = (size_t)ctx->ig.mp[0] * ctx->ig.mp[1] * ctx->ig.mp[2];
     ctx->vpad = (size_t)ctx->vg.mp[0] * ctx->vg.mp[1] * ctx->vg.mp[2];
     ctx->vt_bytes = d == 3 ? 16 : 8;
-    const int tx = d == 3 ? 8 : 16, ty = d == 3 ? 8 : 16, tz = d == 3 ? 4 : 1;
-    ctx->tiles[0] = (ctx->ig.m[0] + tx - 1) / tx;
-    ctx->tiles[1] = (ctx->ig.m[1] + ty - 1) / ty;
-    ctx->tiles[2] = (ctx->ig.m[2] + tz - 1) / tz;
-    ctx->trace_blocks = ctx->tiles[0] * ctx->tiles[1] * ctx->tiles[2];
+    {
+        int ts[3];
+        trace_tile_shape(d, MODE_FWD, false, ts);  // the smallest tile: most blocks, sizes the partial sums
+        for (int i = 0; i < 3; ++i) ctx->tiles[i] = (ctx->ig.m[i] + ts[i] - 1) / ts[i];
+        ctx->trace_blocks = ctx->tiles[0] * ctx->tiles[1] * ctx->tiles[2];
+    }
     double hv = 1.0, hi = 1.0;
     for (int a = 0; a < d; ++a) {
         hi *= (prob->image.hi[a] - prob->image.lo[a]) / prob->image.m[a];

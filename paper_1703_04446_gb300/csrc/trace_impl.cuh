@@ -23,6 +23,16 @@
 // its displacement (an absolute FP32 coordinate would round it away), and the
 // cell choice at the kinks of the piecewise-linear interpolant agrees with an
 // exact evaluation.
+//
+// Jacobian-free derivative products.  d_y I(v, y) enters only as J q (tangent)
+// and J^T mu (adjoint).  Both are accumulated corner by corner from the same
+// gathered corner values: J q = sum_c v(c) (grad w_c . q) and
+// J^T mu = sum_c grad w_c (v(c) . mu), so no d x d matrix lives in registers.
+//
+// Gradient scatter.  For a stationary velocity the adjoint kernels accumulate
+// (d_v I)^T mu in a shared-memory tile of the velocity grid covering the CTA's
+// voxels plus a halo of LGNK_HALO cells; corners outside it go to global
+// atomics.  The tile is flushed with one vector atomic per touched node.
 #pragma once
 
 #include "lgnk_internal.h"
@@ -48,23 +58,21 @@ __device__ __forceinline__ void red_vec(float4* p, const float* x, float w) {
     atomicAdd(p, make_float4(w * x[0], w * x[1], w * x[2], 0.0f));
 }
 
-// Start of one characteristic on one grid: continuous index I0 + F0 and the
-// clamp bounds of the offset t = F0 + u / h that keep I0 + floor(t) in [-2, m].
+// Start of one characteristic on one grid: its continuous grid index I0 + F0.
+// Offsets t = F0 + u / h are clamped to [-2 - I0, m - I0 + 1/2], which keeps
+// the lower corner I0 + floor(t) in [-2, m].
 template <int D>
 struct Start {
     int I0[D];
     float F0[D];
-    float lo[D], hi[D];
 };
 
 template <int D>
-__device__ __forceinline__ void start_on_image(const DevGrid& g, const int* idx, Start<D>& s) {
+__device__ __forceinline__ void start_on_image(const int* idx, Start<D>& s) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         s.I0[a] = idx[a];
         s.F0[a] = 0.0f;
-        s.lo[a] = (float)(-2 - idx[a]);
-        s.hi[a] = (float)(g.m[a] - idx[a]) + 0.5f;
     }
 }
 
@@ -77,27 +85,28 @@ __device__ __forceinline__ void start_on_velocity(const TraceArgs& A, const int*
         const int i0 = (int)fmax(fmin(fl, (double)A.vg.m[a]), -2.0);
         s.I0[a] = i0;
         s.F0[a] = (float)(xi - (double)i0);
-        s.lo[a] = (float)(-2 - i0);
-        s.hi[a] = (float)(A.vg.m[a] - i0) + 0.5f;
     }
 }
 
-// Cell of the point at displacement u from the start: padded linear index of the
-// lower corner and fractional offsets f in [0, 1].  NaN maps to the lowest
-// clamp, so any point addresses padded storage.
+// Cell of the point at displacement u from the start: per-axis padded index p
+// of the lower corner and fractional offsets f in [0, 1].  NaN maps to the
+// lowest clamp, so any point addresses padded storage.
 template <int D>
-__device__ __forceinline__ int locate(const DevGrid& g, const Start<D>& s, const float* u, float* f) {
-    int idx[D];
+__device__ __forceinline__ void locate(const DevGrid& g, const Start<D>& s, const float* u, int* p, float* f) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         float t = fmaf(u[a], g.inv_h[a], s.F0[a]);
-        t = fminf(fmaxf(t, s.lo[a]), s.hi[a]);
+        t = fminf(fmaxf(t, (float)(-2 - s.I0[a])), (float)(g.m[a] - s.I0[a]) + 0.5f);
         const float fl = floorf(t);
         f[a] = t - fl;
-        idx[a] = s.I0[a] + (int)fl + LGNK_PAD;
+        p[a] = s.I0[a] + (int)fl + LGNK_PAD;
     }
-    if (D == 3) return idx[0] + g.mp[0] * (idx[1] + g.mp[1] * idx[2]);
-    return idx[0] + g.mp[0] * idx[1];
+}
+
+template <int D>
+__device__ __forceinline__ int linear(const DevGrid& g, const int* p) {
+    if (D == 3) return p[0] + g.mp[0] * (p[1] + g.mp[1] * p[2]);
+    return p[0] + g.mp[0] * p[1];
 }
 
 template <int D>
@@ -138,72 +147,118 @@ __device__ __forceinline__ void time_slot(int K, float t, int& j, float& th) {
     th = s - (float)jj;
 }
 
-// I(v, p, t) and optionally d_y I (jac[c*D + a] = dV_c/dy_a) and I(dv, p, t).
-template <int D, bool NS, bool JAC, bool DV>
-__device__ __forceinline__ void sample_velocity(const DevGrid& g, int K,
-                                                const typename VecT<D>::type* __restrict__ V,
-                                                const typename VecT<D>::type* __restrict__ dV,
-                                                int base, const float* f, int jt, float th,
-                                                float* val, float* jac, float* dval) {
+template <int D, bool NS>
+__device__ __forceinline__ void corner_value(const typename VecT<D>::type* __restrict__ V, size_t e, float th,
+                                             float* a) {
+    load_vec(V + e, a);
+    if (NS) {
+        float b[D];
+        load_vec(V + e + 1, b);
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-        val[c] = 0.0f;
-        if (DV) dval[c] = 0.0f;
+        for (int q = 0; q < D; ++q) a[q] = fmaf(th, b[q] - a[q], a[q]);
     }
-    if (JAC) {
+}
+
+// val = I(v, y, t).
+template <int D, bool NS>
+__device__ __forceinline__ void stage_value(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
+                                            const int* p, const float* f, int jt, float th, float* val) {
+    const int base = linear<D>(g, p);
 #pragma unroll
-        for (int i = 0; i < D * D; ++i) jac[i] = 0.0f;
+    for (int q = 0; q < D; ++q) val[q] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        float a[D];
+        corner_value<D, NS>(V, (size_t)(base + corner_offset<D>(g, c)) * K + jt, th, a);
+        const float w = corner_weight<D, false>(c, f, g, nullptr);
+#pragma unroll
+        for (int q = 0; q < D; ++q) val[q] = fmaf(w, a[q], val[q]);
+    }
+}
+
+// Tangent stage: val = I(v, y, t), Jq = d_y I(v, y, t) q, dval = I(dv, y, t).
+template <int D, bool NS>
+__device__ __forceinline__ void stage_tangent(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
+                                              const typename VecT<D>::type* __restrict__ dV, const int* p,
+                                              const float* f, int jt, float th, const float* qv, float* val,
+                                              float* Jq, float* dval) {
+    const int base = linear<D>(g, p);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        val[q] = 0.0f;
+        Jq[q] = 0.0f;
+        dval[q] = 0.0f;
     }
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
         const size_t e = (size_t)(base + corner_offset<D>(g, c)) * K + jt;
-        float a[D];
-        load_vec(V + e, a);
-        if (NS) {
-            float b[D];
-            load_vec(V + e + 1, b);
+        float a[D], da[D], dw[D];
+        corner_value<D, NS>(V, e, th, a);
+        corner_value<D, NS>(dV, e, th, da);
+        const float w = corner_weight<D, true>(c, f, g, dw);
+        float s = 0.0f;
 #pragma unroll
-            for (int q = 0; q < D; ++q) a[q] = fmaf(th, b[q] - a[q], a[q]);
-        }
-        float dw[D];
-        const float w = corner_weight<D, JAC>(c, f, g, dw);
+        for (int ax = 0; ax < D; ++ax) s = fmaf(dw[ax], qv[ax], s);
 #pragma unroll
-        for (int q = 0; q < D; ++q) val[q] = fmaf(w, a[q], val[q]);
-        if (JAC) {
-#pragma unroll
-            for (int q = 0; q < D; ++q)
-#pragma unroll
-                for (int ax = 0; ax < D; ++ax) jac[q * D + ax] = fmaf(dw[ax], a[q], jac[q * D + ax]);
-        }
-        if (DV) {
-            float da[D];
-            load_vec(dV + e, da);
-            if (NS) {
-                float db[D];
-                load_vec(dV + e + 1, db);
-#pragma unroll
-                for (int q = 0; q < D; ++q) da[q] = fmaf(th, db[q] - da[q], da[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < D; ++q) dval[q] = fmaf(w, da[q], dval[q]);
+        for (int q = 0; q < D; ++q) {
+            val[q] = fmaf(w, a[q], val[q]);
+            Jq[q] = fmaf(s, a[q], Jq[q]);
+            dval[q] = fmaf(w, da[q], dval[q]);
         }
     }
 }
 
-// G += (d_v I(., p, t))^T mu: the transpose of the velocity interpolation.
+// Destination of the adjoint scatter (d_v I)^T mu: a shared-memory tile of the
+// padded velocity grid (stationary fields) with global atomics as fallback.
+template <int D>
+struct Scatter {
+    typename VecT<D>::type* G;  // padded packed gradient accumulator
+    float* sm;                  // tile, [D][nodes]; nullptr = global only
+    int o[3];                   // tile origin (padded node indices)
+    int E[3];                   // tile extents
+    int n;                      // tile nodes
+};
+
+// Adjoint stage: scatter w_c * (time weight) * mu into the gradient and return
+// nu = d_y I(v, y, t)^T mu.
 template <int D, bool NS>
-__device__ __forceinline__ void scatter_velocity(const DevGrid& g, int K, typename VecT<D>::type* G,
-                                                 int base, const float* f, int jt, float th,
-                                                 const float* mu) {
+__device__ __forceinline__ void stage_adjoint(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
+                                              const Scatter<D>& S, const int* p, const float* f, int jt, float th,
+                                              const float* mu, float* nu) {
+    const int base = linear<D>(g, p);
+    bool in_tile = !NS && S.sm != nullptr;
+    int lb = 0;
+    if (in_tile) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) in_tile = in_tile && p[a] >= S.o[a] && p[a] + 1 < S.o[a] + S.E[a];
+        if (in_tile) {
+            lb = p[0] - S.o[0] + S.E[0] * (p[1] - S.o[1]);
+            if (D == 3) lb += S.E[0] * S.E[1] * (p[2] - S.o[2]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < D; ++q) nu[q] = 0.0f;
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
         const size_t e = (size_t)(base + corner_offset<D>(g, c)) * K + jt;
-        const float w = corner_weight<D, false>(c, f, g, nullptr);
-        if (NS) {
-            red_vec(G + e, mu, w * (1.0f - th));
-            red_vec(G + e + 1, mu, w * th);
+        float a[D], dw[D];
+        corner_value<D, NS>(V, e, th, a);
+        const float w = corner_weight<D, true>(c, f, g, dw);
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < D; ++q) s = fmaf(a[q], mu[q], s);
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) nu[ax] = fmaf(dw[ax], s, nu[ax]);
+        if (in_tile) {
+            int lo = lb + (c & 1) + ((c >> 1) & 1) * S.E[0];
+            if (D == 3) lo += ((c >> 2) & 1) * S.E[0] * S.E[1];
+#pragma unroll
+            for (int q = 0; q < D; ++q) atomicAdd(S.sm + q * S.n + lo, w * mu[q]);
+        } else if (NS) {
+            red_vec(S.G + e, mu, w * (1.0f - th));
+            red_vec(S.G + e + 1, mu, w * th);
         } else {
-            red_vec(G + e, mu, w);
+            red_vec(S.G + e, mu, w);
         }
     }
 }
@@ -212,8 +267,10 @@ __device__ __forceinline__ void scatter_velocity(const DevGrid& g, int K, typena
 template <int D, bool GRAD>
 __device__ __forceinline__ float sample_image(const DevGrid& g, const Start<D>& s, const float* __restrict__ Tp,
                                               const float* u, float* grad) {
+    int p[D];
     float f[D];
-    const int base = locate<D>(g, s, u, f);
+    locate<D>(g, s, u, p, f);
+    const int base = linear<D>(g, p);
     float val = 0.0f;
     if (GRAD) {
 #pragma unroll
@@ -237,8 +294,10 @@ __device__ __forceinline__ float sample_image(const DevGrid& g, const Start<D>& 
 template <int D, bool TANGENT>
 __device__ __forceinline__ void splat_image(const DevGrid& g, const Start<D>& s, float* acc, const float* u,
                                             float mass, const float* dp) {
+    int p[D];
     float f[D];
-    const int base = locate<D>(g, s, u, f);
+    locate<D>(g, s, u, p, f);
+    const int base = linear<D>(g, p);
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
         float dw[D];
@@ -256,57 +315,45 @@ __device__ __forceinline__ void splat_image(const DevGrid& g, const Start<D>& s,
     }
 }
 
+struct Slots {
+    int j1, j2, j4;
+    float th1, th2, th4;
+};
+
+__device__ __forceinline__ Slots step_slots(const TraceArgs& A, float tk) {
+    Slots s;
+    time_slot(A.K, tk, s.j1, s.th1);
+    time_slot(A.K, tk + 0.5f * A.dt, s.j2, s.th2);
+    time_slot(A.K, tk + A.dt, s.j4, s.th4);
+    return s;
+}
+
 // One RK4 step of the characteristic (Alg. 1 without the derivative), on the
 // displacement u.
 template <int D, bool NS>
 __device__ __forceinline__ void rk4_step(const TraceArgs& A, const Start<D>& sv,
                                          const typename VecT<D>::type* V, float* u, float tk) {
-    int j1, j2, j4;
-    float th1, th2, th4;
-    time_slot(A.K, tk, j1, th1);
-    time_slot(A.K, tk + 0.5f * A.dt, j2, th2);
-    time_slot(A.K, tk + A.dt, j4, th4);
+    const Slots sl = step_slots(A, tk);
     const float dt = A.dt, hdt = 0.5f * A.dt;
-    float f[D], v1[D], v2[D], v3[D], v4[D], us[D];
-    int b = locate<D>(A.vg, sv, u, f);
-    sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j1, th1, v1, nullptr, nullptr);
+    int p[D];
+    float f[D], vs[D], us[D], acc[D];
+    locate<D>(A.vg, sv, u, p, f);
+    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j1, sl.th1, vs);
 #pragma unroll
-    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, v1[a], u[a]);
-    b = locate<D>(A.vg, sv, us, f);
-    sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j2, th2, v2, nullptr, nullptr);
+    for (int a = 0; a < D; ++a) { acc[a] = vs[a]; us[a] = fmaf(hdt, vs[a], u[a]); }
+    locate<D>(A.vg, sv, us, p, f);
+    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
 #pragma unroll
-    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, v2[a], u[a]);
-    b = locate<D>(A.vg, sv, us, f);
-    sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j2, th2, v3, nullptr, nullptr);
+    for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(hdt, vs[a], u[a]); }
+    locate<D>(A.vg, sv, us, p, f);
+    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
 #pragma unroll
-    for (int a = 0; a < D; ++a) us[a] = fmaf(dt, v3[a], u[a]);
-    b = locate<D>(A.vg, sv, us, f);
-    sample_velocity<D, NS, false, false>(A.vg, A.K, V, nullptr, b, f, j4, th4, v4, nullptr, nullptr);
+    for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(dt, vs[a], u[a]); }
+    locate<D>(A.vg, sv, us, p, f);
+    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j4, sl.th4, vs);
     const float s6 = dt / 6.0f;
 #pragma unroll
-    for (int a = 0; a < D; ++a) u[a] = fmaf(s6, v1[a] + 2.0f * (v2[a] + v3[a]) + v4[a], u[a]);
-}
-
-template <int D>
-__device__ __forceinline__ void matvec(const float* J, const float* x, float* out) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        float s = 0.0f;
-#pragma unroll
-        for (int a = 0; a < D; ++a) s = fmaf(J[c * D + a], x[a], s);
-        out[c] = s;
-    }
-}
-
-template <int D>
-__device__ __forceinline__ void rmatvec(const float* J, const float* x, float* out) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        float s = 0.0f;
-#pragma unroll
-        for (int c = 0; c < D; ++c) s = fmaf(J[c * D + a], x[c], s);
-        out[a] = s;
-    }
+    for (int a = 0; a < D; ++a) u[a] = fmaf(s6, acc[a] + vs[a], u[a]);
 }
 
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
@@ -316,111 +363,108 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const Start
                                                  const typename VecT<D>::type* V,
                                                  const typename VecT<D>::type* dV, float* u, float* dy,
                                                  float tk) {
-    int j1, j2, j4;
-    float th1, th2, th4;
-    time_slot(A.K, tk, j1, th1);
-    time_slot(A.K, tk + 0.5f * A.dt, j2, th2);
-    time_slot(A.K, tk + A.dt, j4, th4);
+    const Slots sl = step_slots(A, tk);
     const float dt = A.dt, hdt = 0.5f * A.dt;
-    float f[D], us[D], q[D], J[D * D], dvs[D], Jq[D];
-    float v1[D], v2[D], v3[D], v4[D], D1[D], D2[D], D3[D], D4[D];
-
-    int b = locate<D>(A.vg, sv, u, f);
-    sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j1, th1, v1, J, dvs);
-    matvec<D>(J, dy, Jq);
+    int p[D];
+    float f[D], us[D], q[D], vs[D], Jq[D], dvs[D], sv_acc[D], sd_acc[D], Ds;
+    // stage 1 at y, offset dy
+    locate<D>(A.vg, sv, u, p, f);
+    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j1, sl.th1, dy, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        D1[a] = dvs[a] + Jq[a];
-        us[a] = fmaf(hdt, v1[a], u[a]);
-        q[a] = fmaf(hdt, D1[a], dy[a]);
+        Ds = dvs[a] + Jq[a];
+        sv_acc[a] = vs[a];
+        sd_acc[a] = Ds;
+        us[a] = fmaf(hdt, vs[a], u[a]);
+        q[a] = fmaf(hdt, Ds, dy[a]);
     }
-    b = locate<D>(A.vg, sv, us, f);
-    sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j2, th2, v2, J, dvs);
-    matvec<D>(J, q, Jq);
+    // stage 2
+    locate<D>(A.vg, sv, us, p, f);
+    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j2, sl.th2, q, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        D2[a] = dvs[a] + Jq[a];
-        us[a] = fmaf(hdt, v2[a], u[a]);
-        q[a] = fmaf(hdt, D2[a], dy[a]);
+        Ds = dvs[a] + Jq[a];
+        sv_acc[a] = fmaf(2.0f, vs[a], sv_acc[a]);
+        sd_acc[a] = fmaf(2.0f, Ds, sd_acc[a]);
+        us[a] = fmaf(hdt, vs[a], u[a]);
+        q[a] = fmaf(hdt, Ds, dy[a]);
     }
-    b = locate<D>(A.vg, sv, us, f);
-    sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j2, th2, v3, J, dvs);
-    matvec<D>(J, q, Jq);
+    // stage 3
+    locate<D>(A.vg, sv, us, p, f);
+    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j2, sl.th2, q, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        D3[a] = dvs[a] + Jq[a];
-        us[a] = fmaf(dt, v3[a], u[a]);
-        q[a] = fmaf(dt, D3[a], dy[a]);
+        Ds = dvs[a] + Jq[a];
+        sv_acc[a] = fmaf(2.0f, vs[a], sv_acc[a]);
+        sd_acc[a] = fmaf(2.0f, Ds, sd_acc[a]);
+        us[a] = fmaf(dt, vs[a], u[a]);
+        q[a] = fmaf(dt, Ds, dy[a]);
     }
-    b = locate<D>(A.vg, sv, us, f);
-    sample_velocity<D, NS, true, true>(A.vg, A.K, V, dV, b, f, j4, th4, v4, J, dvs);
-    matvec<D>(J, q, Jq);
+    // stage 4
+    locate<D>(A.vg, sv, us, p, f);
+    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j4, sl.th4, q, vs, Jq, dvs);
     const float s6 = dt / 6.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        D4[a] = dvs[a] + Jq[a];
-        dy[a] = fmaf(s6, D1[a] + 2.0f * (D2[a] + D3[a]) + D4[a], dy[a]);
-        u[a] = fmaf(s6, v1[a] + 2.0f * (v2[a] + v3[a]) + v4[a], u[a]);
+        dy[a] = fmaf(s6, sd_acc[a] + dvs[a] + Jq[a], dy[a]);
+        u[a] = fmaf(s6, sv_acc[a] + vs[a], u[a]);
     }
 }
 
 // Transpose of one tangent step: given lam (adjoint of the step's end point),
-// scatter the step's contribution into G and return the adjoint of its start.
+// scatter the step's contribution into the gradient and return the adjoint of
+// its start.  Stage positions are recomputed from the step start u; each
+// stage's J^T mu and scatter share one pass over its corners.
 template <int D, bool NS>
 __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const Start<D>& sv,
-                                                 const typename VecT<D>::type* V, typename VecT<D>::type* G,
+                                                 const typename VecT<D>::type* V, const Scatter<D>& S,
                                                  const float* u, float* lam, float tk) {
-    int j1, j2, j4;
-    float th1, th2, th4;
-    time_slot(A.K, tk, j1, th1);
-    time_slot(A.K, tk + 0.5f * A.dt, j2, th2);
-    time_slot(A.K, tk + A.dt, j4, th4);
+    const Slots sl = step_slots(A, tk);
     const float dt = A.dt, hdt = 0.5f * A.dt;
-    float f1[D], f2[D], f3[D], f4[D], J1[D * D], J2[D * D], J3[D * D], J4[D * D];
-    float vs[D], us[D];
-    const int b1 = locate<D>(A.vg, sv, u, f1);
-    sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b1, f1, j1, th1, vs, J1, nullptr);
+    int p[D];
+    float f[D], vs[D], u2[D], u3[D], u4[D];
+    locate<D>(A.vg, sv, u, p, f);
+    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j1, sl.th1, vs);
 #pragma unroll
-    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, vs[a], u[a]);
-    const int b2 = locate<D>(A.vg, sv, us, f2);
-    sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b2, f2, j2, th2, vs, J2, nullptr);
+    for (int a = 0; a < D; ++a) u2[a] = fmaf(hdt, vs[a], u[a]);
+    locate<D>(A.vg, sv, u2, p, f);
+    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
 #pragma unroll
-    for (int a = 0; a < D; ++a) us[a] = fmaf(hdt, vs[a], u[a]);
-    const int b3 = locate<D>(A.vg, sv, us, f3);
-    sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b3, f3, j2, th2, vs, J3, nullptr);
+    for (int a = 0; a < D; ++a) u3[a] = fmaf(hdt, vs[a], u[a]);
+    locate<D>(A.vg, sv, u3, p, f);
+    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
 #pragma unroll
-    for (int a = 0; a < D; ++a) us[a] = fmaf(dt, vs[a], u[a]);
-    const int b4 = locate<D>(A.vg, sv, us, f4);
-    sample_velocity<D, NS, true, false>(A.vg, A.K, V, nullptr, b4, f4, j4, th4, vs, J4, nullptr);
+    for (int a = 0; a < D; ++a) u4[a] = fmaf(dt, vs[a], u[a]);
 
     float mu[D], nu[D], acc[D];
     const float c16 = dt / 6.0f, c13 = dt / 3.0f;
+    // stage 4: D4 = I(dv, y4) + J4 (dy + dt D3)
 #pragma unroll
     for (int a = 0; a < D; ++a) mu[a] = c16 * lam[a];
-    scatter_velocity<D, NS>(A.vg, A.K, G, b4, f4, j4, th4, mu);
-    rmatvec<D>(J4, mu, nu);
+    locate<D>(A.vg, sv, u4, p, f);
+    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j4, sl.th4, mu, nu);
+    // stage 3: D3 = I(dv, y3) + J3 (dy + dt/2 D2)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); }
-    scatter_velocity<D, NS>(A.vg, A.K, G, b3, f3, j2, th2, mu);
-    rmatvec<D>(J3, mu, nu);
+    locate<D>(A.vg, sv, u3, p, f);
+    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j2, sl.th2, mu, nu);
+    // stage 2: D2 = I(dv, y2) + J2 (dy + dt/2 D1)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); }
-    scatter_velocity<D, NS>(A.vg, A.K, G, b2, f2, j2, th2, mu);
-    rmatvec<D>(J2, mu, nu);
+    locate<D>(A.vg, sv, u2, p, f);
+    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j2, sl.th2, mu, nu);
+    // stage 1: D1 = I(dv, y) + J1 dy
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); }
-    scatter_velocity<D, NS>(A.vg, A.K, G, b1, f1, j1, th1, mu);
-    rmatvec<D>(J1, mu, nu);
+    locate<D>(A.vg, sv, u, p, f);
+    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j1, sl.th1, mu, nu);
 #pragma unroll
     for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
 }
 
-template <int D> struct Tile;
-template <> struct Tile<2> { static constexpr int X = 16, Y = 16, Z = 1; };
-template <> struct Tile<3> { static constexpr int X = 8, Y = 8, Z = 4; };
-
 __device__ __forceinline__ double block_sum(double x) {
-    __shared__ double red[LGNK_BLOCK / 32];
+    __shared__ double red[32];
+    const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -428,21 +472,32 @@ __device__ __forceinline__ double block_sum(double x) {
     __syncthreads();
     double s = 0.0;
     if (warp == 0) {
-        s = (lane < LGNK_BLOCK / 32) ? red[lane] : 0.0;
+        s = (lane < nw) ? red[lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     }
     return s;
 }
 
+template <int D> struct TileShape;
+template <> struct TileShape<2> {
+    template <bool BIG> struct S { static constexpr int X = BIG ? 32 : 16, Y = 16, Z = 1; };
+};
+template <> struct TileShape<3> {
+    template <bool BIG> struct S { static constexpr int X = 8, Y = 8, Z = BIG ? 8 : 4; };
+};
+
 template <int D, bool NS, int MODEL, int MODE>
-__global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
+__global__ void __launch_bounds__(trace_big_tile(MODE, NS) ? 512 : 256,
+                                   trace_big_tile(MODE, NS) ? 2 : (trace_mode_adjoint(MODE) ? 2 : 4))
+    trace_kernel(const TraceArgs A) {
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
     constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD);
+    using TS = typename TileShape<D>::template S<trace_big_tile(MODE, NS)>;
+    extern __shared__ float smem[];
     const VT* V = static_cast<const VT*>(A.V);
     const VT* dV = static_cast<const VT*>(A.dV);
-    VT* G = static_cast<VT*>(A.G);
 
     int b = blockIdx.x;
     const int bx = b % A.tiles[0];
@@ -450,17 +505,43 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
     const int by = b % A.tiles[1];
     const int bz = b / A.tiles[1];
     const int t = threadIdx.x;
+    const int v0[3] = {bx * TS::X, by * TS::Y, bz * TS::Z};
     int idx[3];
-    idx[0] = bx * Tile<D>::X + t % Tile<D>::X;
-    idx[1] = by * Tile<D>::Y + (t / Tile<D>::X) % Tile<D>::Y;
-    idx[2] = bz * Tile<D>::Z + t / (Tile<D>::X * Tile<D>::Y);
+    idx[0] = v0[0] + t % TS::X;
+    idx[1] = v0[1] + (t / TS::X) % TS::Y;
+    idx[2] = v0[2] + t / (TS::X * TS::Y);
     const bool active = idx[0] < A.ig.m[0] && idx[1] < A.ig.m[1] && (D == 2 || idx[2] < A.ig.m[2]);
     double ssd = 0.0;
 
+    Scatter<D> S;
+    S.G = static_cast<VT*>(A.G);
+    S.sm = nullptr;
+    S.n = 0;
+    if (ADJOINT && !NS && A.sm_bytes > 0) {
+        // tile of padded velocity nodes covering this CTA's start cells plus the halo
+        const int ext[3] = {TS::X, TS::Y, TS::Z};
+        int n = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const double xlo = A.vxi_a[a] + ((double)v0[a] + 0.5) * A.vxi_b[a];
+            int lo = (int)floor(xlo) - LGNK_HALO + LGNK_PAD;
+            lo = max(lo, 0);
+            lo = min(lo, A.vg.mp[a] - 1);
+            const int E = min(A.smE[a], A.vg.mp[a] - lo);
+            S.o[a] = lo;
+            S.E[a] = E;
+            n *= E;
+            (void)ext;
+        }
+        S.n = n;
+        S.sm = smem;
+        for (int i = t; i < n * D; i += blockDim.x) smem[i] = 0.0f;
+        __syncthreads();
+    }
+
     if (active) {
         const int vox = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
-        Start<D> si, sv;
-        start_on_image<D>(A.ig, idx, si);
+        Start<D> sv;
         start_on_velocity<D>(A, idx, sv);
         float u[D], dy[D];
 #pragma unroll
@@ -489,6 +570,8 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
         }
 
         float lam[D];
+        Start<D> si;
+        start_on_image<D>(idx, si);
         if (MODEL == LGNK_TRANSPORT) {
             float gT[D];
             if (MODE == MODE_FWD) {
@@ -543,8 +626,28 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
         if (ADJOINT) {
             for (int k = A.N - 1; k >= 0; --k) {
                 const float tk = A.t0 + (float)k * A.dt;
-                rk4_adjoint_step<D, NS>(A, sv, V, G, hist[ADJOINT ? k : 0], lam, tk);
+                rk4_adjoint_step<D, NS>(A, sv, V, S, hist[ADJOINT ? k : 0], lam, tk);
             }
+        }
+    }
+
+    if (ADJOINT && S.sm != nullptr) {
+        // flush the tile: one vector atomic per touched node (stationary: K = 1)
+        __syncthreads();
+        for (int i = t; i < S.n; i += blockDim.x) {
+            float val[D];
+            bool nz = false;
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                val[q] = S.sm[q * S.n + i];
+                nz = nz || val[q] != 0.0f;
+            }
+            if (!nz) continue;
+            int pp[3];
+            pp[0] = S.o[0] + i % S.E[0];
+            pp[1] = S.o[1] + (i / S.E[0]) % S.E[1];
+            pp[2] = (D == 3) ? S.o[2] + i / (S.E[0] * S.E[1]) : 0;
+            red_vec(S.G + linear<D>(A.vg, pp), val, 1.0f);
         }
     }
 
@@ -557,8 +660,28 @@ __global__ void __launch_bounds__(LGNK_BLOCK) trace_kernel(const TraceArgs A) {
 }
 
 template <int D, bool NS, int MODEL, int MODE>
-static cudaError_t launch_one(const TraceArgs& a, int nblocks, cudaStream_t s) {
-    trace_kernel<D, NS, MODEL, MODE><<<nblocks, LGNK_BLOCK, 0, s>>>(a);
+static cudaError_t launch_one(const TraceArgs& a0, int nblocks, cudaStream_t s) {
+    (void)nblocks;
+    TraceArgs a = a0;
+    int ts[3];
+    trace_tile_shape(D, MODE, NS, ts);
+    for (int i = 0; i < 3; ++i) a.tiles[i] = (a.ig.m[i] + ts[i] - 1) / ts[i];
+    const int blocks = a.tiles[0] * a.tiles[1] * a.tiles[2];
+    const int threads = ts[0] * ts[1] * ts[2];
+    size_t smem = 0;
+    if (trace_mode_adjoint(MODE) && !NS && a.sm_bytes > 0) {
+        smem = (size_t)a.sm_bytes;
+        static bool attr_set = false;
+        if (!attr_set && smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(trace_kernel<D, NS, MODEL, MODE>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, LGNK_TILE_SMEM_MAX);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+    } else {
+        a.sm_bytes = 0;
+    }
+    trace_kernel<D, NS, MODEL, MODE><<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
