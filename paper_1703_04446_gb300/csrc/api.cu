@@ -184,22 +184,6 @@ TraceArgs base_args(const lgnk_ctx* ctx) {
             a.vxi_b[i] = 0.0;
         }
     }
-    // shared-memory gradient tile of the adjoint kernels (stationary fields)
-    a.sm_bytes = 0;
-    if (ctx->K == 1) {
-        int ts[3];
-        trace_tile_shape(ctx->d, MODE_HESS, false, ts);
-        size_t nodes = 1;
-        for (int i = 0; i < 3; ++i) {
-            a.smE[i] = 1;
-            if (i < ctx->d) {
-                a.smE[i] = (int)std::floor((ts[i] - 1) * a.vxi_b[i]) + 3 + 2 * LGNK_HALO;
-                nodes *= (size_t)a.smE[i];
-            }
-        }
-        const size_t bytes = nodes * ctx->d * sizeof(float);
-        if (bytes <= LGNK_TILE_SMEM_MAX) a.sm_bytes = (int)bytes;
-    }
     a.V = ctx->Vp;
     a.dV = ctx->dVp;
     a.Tp = ctx->Tp;
@@ -219,7 +203,8 @@ lgnk_status record_event(lgnk_ctx* ctx) {
 
 int trace_blocks_for(const lgnk_ctx* ctx, int mode) {
     int ts[3];
-    trace_tile_shape(ctx->d, mode, ctx->K > 1, ts);
+    (void)mode;
+    trace_tile_shape(ctx->d, ts);
     int n = 1;
     for (int i = 0; i < 3; ++i) n *= (ctx->ig.m[i] + ts[i] - 1) / ts[i];
     return n;
@@ -503,7 +488,7 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     ctx->vt_bytes = d == 3 ? 16 : 8;
     {
         int ts[3];
-        trace_tile_shape(d, MODE_FWD, false, ts);  // the smallest tile: most blocks, sizes the partial sums
+        trace_tile_shape(d, ts);
         for (int i = 0; i < 3; ++i) ctx->tiles[i] = (ctx->ig.m[i] + ts[i] - 1) / ts[i];
         ctx->trace_blocks = ctx->tiles[0] * ctx->tiles[1] * ctx->tiles[2];
     }

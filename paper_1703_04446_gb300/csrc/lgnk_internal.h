@@ -15,10 +15,6 @@
 #define LGNK_PAD 2
 #define LGNK_MAX_STEPS 64
 #define LGNK_BLOCK 256
-// Halo (velocity cells) of the shared-memory gradient tile of the adjoint kernels.
-#define LGNK_HALO 4
-// Upper bound on that tile's bytes; larger tiles fall back to global atomics.
-#define LGNK_TILE_SMEM_MAX (64 * 1024)
 
 struct DevGrid {
     int m[3];      // cells per axis (1 for an absent axis)
@@ -30,20 +26,10 @@ struct DevGrid {
 
 enum TraceMode { MODE_FWD = 0, MODE_JVP = 1, MODE_JTVP = 2, MODE_HESS = 3, MODE_OBJGRAD = 4 };
 
-// Voxel tile of one CTA of the tracing kernels (x, y, z).  The adjoint modes
-// (JTVP, HESS, OBJGRAD) of a stationary velocity use the larger 512-thread
-// tile, which amortises their shared-memory gradient tile over more
-// characteristics; everything else runs 256-thread tiles.
-__host__ __device__ constexpr inline bool trace_mode_adjoint(int mode) {
-    return mode == MODE_JTVP || mode == MODE_HESS || mode == MODE_OBJGRAD;
-}
-__host__ __device__ constexpr inline bool trace_big_tile(int mode, bool nonstat) {
-    return trace_mode_adjoint(mode) && !nonstat;
-}
-inline void trace_tile_shape(int d, int mode, bool nonstat, int* t) {
-    const bool big = trace_big_tile(mode, nonstat);
-    if (d == 3) { t[0] = 8; t[1] = 8; t[2] = big ? 8 : 4; }
-    else { t[0] = big ? 32 : 16; t[1] = 16; t[2] = 1; }
+// Voxel tile of one 256-thread CTA of the tracing kernels (x, y, z).
+inline void trace_tile_shape(int d, int* t) {
+    if (d == 3) { t[0] = 8; t[1] = 8; t[2] = 4; }
+    else { t[0] = 16; t[1] = 16; t[2] = 1; }
 }
 
 // Arguments of one launch of the characteristic-tracing kernel family.
@@ -53,8 +39,6 @@ struct TraceArgs {
     float dt, t0;
     float cellvol;            // image cell volume h^d (SSD weight)
     int tiles[3];             // voxel tiles per axis (grid = product), set per launch
-    int smE[3];               // max extents (padded velocity nodes) of the gradient tile
-    int sm_bytes;             // its dynamic shared memory; 0 = global atomics only
     // continuous velocity-grid index of the start point of voxel i along axis a:
     // vxi_a[a] + (i + 1/2) * vxi_b[a]  (exact in FP64: (x_c - lo_v) / h_v - 1/2)
     double vxi_a[3], vxi_b[3];

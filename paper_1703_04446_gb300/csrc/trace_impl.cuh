@@ -25,14 +25,17 @@
 // exact evaluation.
 //
 // Jacobian-free derivative products.  d_y I(v, y) enters only as J q (tangent)
-// and J^T mu (adjoint).  Both are accumulated corner by corner from the same
-// gathered corner values: J q = sum_c v(c) (grad w_c . q) and
-// J^T mu = sum_c grad w_c (v(c) . mu), so no d x d matrix lives in registers.
+// and J^T mu (adjoint).  The interpolant is evaluated separably, one plane of
+// four corners at a time (x then y lerps, then z): the same lerps give the
+// value and the three axis derivatives, J q contracts them with q, and J^T mu
+// is the gradient of the scalar interpolant of v . mu (corners contracted with
+// mu first).  No d x d matrix lives in registers.
 //
-// Gradient scatter.  For a stationary velocity the adjoint kernels accumulate
-// (d_v I)^T mu in a shared-memory tile of the velocity grid covering the CTA's
-// voxels plus a halo of LGNK_HALO cells; corners outside it go to global
-// atomics.  The tile is flushed with one vector atomic per touched node.
+// Gradient scatter.  (d_v I)^T mu goes to the padded gradient accumulator with
+// one vector reduction (red.global.add.v4.f32 / .v2) per corner, executed by
+// the L2 atomic units.  A shared-memory tile of the velocity grid was measured
+// slower: float atomics on shared memory retry under the heavy same-address
+// contention of neighbouring characteristics.
 #pragma once
 
 #include "lgnk_internal.h"
@@ -159,20 +162,71 @@ __device__ __forceinline__ void corner_value(const typename VecT<D>::type* __res
     }
 }
 
-// val = I(v, y, t).
+__device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+// Element index of corner (cx, cy, cz) of the cell with lower corner `base`.
+template <int D>
+__device__ __forceinline__ size_t corner_elem(const DevGrid& g, int base, int cx, int cy, int cz, int K, int jt) {
+    int o = base + cx + cy * g.mp[0];
+    if (D == 3) o += cz * g.mp[0] * g.mp[1];
+    return (size_t)o * K + jt;
+}
+
+// One plane (fixed z corner) of the cell: bilinear value and the unscaled
+// derivatives along the fractional x and y offsets, per component.
+template <int D, bool NS, bool GRAD>
+__device__ __forceinline__ void plane(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V, int base,
+                                      int cz, int jt, float th, const float* f, float* val, float* dx, float* dy) {
+    float c00[D], c10[D], c01[D], c11[D];
+    corner_value<D, NS>(V, corner_elem<D>(g, base, 0, 0, cz, K, jt), th, c00);
+    corner_value<D, NS>(V, corner_elem<D>(g, base, 1, 0, cz, K, jt), th, c10);
+    corner_value<D, NS>(V, corner_elem<D>(g, base, 0, 1, cz, K, jt), th, c01);
+    corner_value<D, NS>(V, corner_elem<D>(g, base, 1, 1, cz, K, jt), th, c11);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const float a0 = lerp(c00[q], c10[q], f[0]);
+        const float a1 = lerp(c01[q], c11[q], f[0]);
+        val[q] = lerp(a0, a1, f[1]);
+        if (GRAD) {
+            dx[q] = lerp(c10[q] - c00[q], c11[q] - c01[q], f[1]);
+            dy[q] = a1 - a0;
+        }
+    }
+}
+
+// Scalar version: corner values contracted with mu first (s_c = v_c . mu).
+template <int D, bool NS>
+__device__ __forceinline__ void plane_dot(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
+                                          int base, int cz, int jt, float th, const float* f, const float* mu,
+                                          float& val, float& dx, float& dy) {
+    float c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float a[D];
+        corner_value<D, NS>(V, corner_elem<D>(g, base, k & 1, k >> 1, cz, K, jt), th, a);
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < D; ++q) s = fmaf(a[q], mu[q], s);
+        c[k] = s;
+    }
+    const float a0 = lerp(c[0], c[1], f[0]);
+    const float a1 = lerp(c[2], c[3], f[0]);
+    val = lerp(a0, a1, f[1]);
+    dx = lerp(c[1] - c[0], c[3] - c[2], f[1]);
+    dy = a1 - a0;
+}
+
+// val = I(v, y, t) (Sec. 3.1, Step 1: multilinear in space, linear in time).
 template <int D, bool NS>
 __device__ __forceinline__ void stage_value(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
                                             const int* p, const float* f, int jt, float th, float* val) {
     const int base = linear<D>(g, p);
+    plane<D, NS, false>(g, K, V, base, 0, jt, th, f, val, nullptr, nullptr);
+    if (D == 3) {
+        float v1[D];
+        plane<D, NS, false>(g, K, V, base, 1, jt, th, f, v1, nullptr, nullptr);
 #pragma unroll
-    for (int q = 0; q < D; ++q) val[q] = 0.0f;
-#pragma unroll
-    for (int c = 0; c < (1 << D); ++c) {
-        float a[D];
-        corner_value<D, NS>(V, (size_t)(base + corner_offset<D>(g, c)) * K + jt, th, a);
-        const float w = corner_weight<D, false>(c, f, g, nullptr);
-#pragma unroll
-        for (int q = 0; q < D; ++q) val[q] = fmaf(w, a[q], val[q]);
+        for (int q = 0; q < D; ++q) val[q] = lerp(val[q], v1[q], f[D - 1]);
     }
 }
 
@@ -183,78 +237,64 @@ __device__ __forceinline__ void stage_tangent(const DevGrid& g, int K, const typ
                                               const float* f, int jt, float th, const float* qv, float* val,
                                               float* Jq, float* dval) {
     const int base = linear<D>(g, p);
+    float qs[D];
 #pragma unroll
-    for (int q = 0; q < D; ++q) {
-        val[q] = 0.0f;
-        Jq[q] = 0.0f;
-        dval[q] = 0.0f;
-    }
-#pragma unroll
-    for (int c = 0; c < (1 << D); ++c) {
-        const size_t e = (size_t)(base + corner_offset<D>(g, c)) * K + jt;
-        float a[D], da[D], dw[D];
-        corner_value<D, NS>(V, e, th, a);
-        corner_value<D, NS>(dV, e, th, da);
-        const float w = corner_weight<D, true>(c, f, g, dw);
-        float s = 0.0f;
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) s = fmaf(dw[ax], qv[ax], s);
+    for (int a = 0; a < D; ++a) qs[a] = qv[a] * g.inv_h[a];
+    float dx[D], dy[D];
+    plane<D, NS, true>(g, K, V, base, 0, jt, th, f, val, dx, dy);
+    if (D == 3) {
+        float v1[D], dx1[D], dy1[D];
+        plane<D, NS, true>(g, K, V, base, 1, jt, th, f, v1, dx1, dy1);
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-            val[q] = fmaf(w, a[q], val[q]);
-            Jq[q] = fmaf(s, a[q], Jq[q]);
-            dval[q] = fmaf(w, da[q], dval[q]);
+            const float dz = v1[q] - val[q];
+            Jq[q] = dz * qs[D - 1];
+            val[q] = lerp(val[q], v1[q], f[D - 1]);
+            dx[q] = lerp(dx[q], dx1[q], f[D - 1]);
+            dy[q] = lerp(dy[q], dy1[q], f[D - 1]);
         }
+    } else {
+#pragma unroll
+        for (int q = 0; q < D; ++q) Jq[q] = 0.0f;
     }
+#pragma unroll
+    for (int q = 0; q < D; ++q) Jq[q] = fmaf(dx[q], qs[0], fmaf(dy[q], qs[1], Jq[q]));
+    stage_value<D, NS>(g, K, dV, p, f, jt, th, dval);
 }
 
-// Destination of the adjoint scatter (d_v I)^T mu: a shared-memory tile of the
-// padded velocity grid (stationary fields) with global atomics as fallback.
+// Destination of the adjoint scatter (d_v I)^T mu: the padded gradient accumulator.
 template <int D>
 struct Scatter {
-    typename VecT<D>::type* G;  // padded packed gradient accumulator
-    float* sm;                  // tile, [D][nodes]; nullptr = global only
-    int o[3];                   // tile origin (padded node indices)
-    int E[3];                   // tile extents
-    int n;                      // tile nodes
+    typename VecT<D>::type* G;
 };
 
 // Adjoint stage: scatter w_c * (time weight) * mu into the gradient and return
-// nu = d_y I(v, y, t)^T mu.
+// nu = d_y I(v, y, t)^T mu = grad_y (v . mu) of the interpolant.
 template <int D, bool NS>
 __device__ __forceinline__ void stage_adjoint(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
                                               const Scatter<D>& S, const int* p, const float* f, int jt, float th,
                                               const float* mu, float* nu) {
     const int base = linear<D>(g, p);
-    bool in_tile = !NS && S.sm != nullptr;
-    int lb = 0;
-    if (in_tile) {
-#pragma unroll
-        for (int a = 0; a < D; ++a) in_tile = in_tile && p[a] >= S.o[a] && p[a] + 1 < S.o[a] + S.E[a];
-        if (in_tile) {
-            lb = p[0] - S.o[0] + S.E[0] * (p[1] - S.o[1]);
-            if (D == 3) lb += S.E[0] * S.E[1] * (p[2] - S.o[2]);
-        }
+    float s0, dx, dy;
+    plane_dot<D, NS>(g, K, V, base, 0, jt, th, f, mu, s0, dx, dy);
+    if (D == 3) {
+        float s1, dx1, dy1;
+        plane_dot<D, NS>(g, K, V, base, 1, jt, th, f, mu, s1, dx1, dy1);
+        nu[D - 1] = (s1 - s0) * g.inv_h[D - 1];
+        dx = lerp(dx, dx1, f[D - 1]);
+        dy = lerp(dy, dy1, f[D - 1]);
     }
-#pragma unroll
-    for (int q = 0; q < D; ++q) nu[q] = 0.0f;
+    nu[0] = dx * g.inv_h[0];
+    nu[1] = dy * g.inv_h[1];
+    // scatter with the multilinear weights
+    const float wx[2] = {1.0f - f[0], f[0]};
+    const float wy[2] = {1.0f - f[1], f[1]};
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
-        const size_t e = (size_t)(base + corner_offset<D>(g, c)) * K + jt;
-        float a[D], dw[D];
-        corner_value<D, NS>(V, e, th, a);
-        const float w = corner_weight<D, true>(c, f, g, dw);
-        float s = 0.0f;
-#pragma unroll
-        for (int q = 0; q < D; ++q) s = fmaf(a[q], mu[q], s);
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) nu[ax] = fmaf(dw[ax], s, nu[ax]);
-        if (in_tile) {
-            int lo = lb + (c & 1) + ((c >> 1) & 1) * S.E[0];
-            if (D == 3) lo += ((c >> 2) & 1) * S.E[0] * S.E[1];
-#pragma unroll
-            for (int q = 0; q < D; ++q) atomicAdd(S.sm + q * S.n + lo, w * mu[q]);
-        } else if (NS) {
+        float w = wx[c & 1] * wy[(c >> 1) & 1];
+        if (D == 3) w *= ((c >> 2) & 1) ? f[D - 1] : 1.0f - f[D - 1];
+        const size_t e = corner_elem<D>(g, base, c & 1, (c >> 1) & 1, (c >> 2) & 1, K, jt);
+        if (NS) {
             red_vec(S.G + e, mu, w * (1.0f - th));
             red_vec(S.G + e + 1, mu, w * th);
         } else {
@@ -480,22 +520,19 @@ __device__ __forceinline__ double block_sum(double x) {
 }
 
 template <int D> struct TileShape;
-template <> struct TileShape<2> {
-    template <bool BIG> struct S { static constexpr int X = BIG ? 32 : 16, Y = 16, Z = 1; };
-};
-template <> struct TileShape<3> {
-    template <bool BIG> struct S { static constexpr int X = 8, Y = 8, Z = BIG ? 8 : 4; };
-};
+template <> struct TileShape<2> { static constexpr int X = 16, Y = 16, Z = 1; };
+template <> struct TileShape<3> { static constexpr int X = 8, Y = 8, Z = 4; };
 
 template <int D, bool NS, int MODEL, int MODE>
-__global__ void __launch_bounds__(trace_big_tile(MODE, NS) ? 512 : 256,
-                                   trace_big_tile(MODE, NS) ? 2 : (trace_mode_adjoint(MODE) ? 2 : 4))
+// 256 threads; FWD at 64 registers (4 CTAs per SM), the derivative modes at 80
+// (3 CTAs): measured fastest among 64/80/128-register and 256/512-thread
+// configurations on the 128^3 matvec.
+__global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
     trace_kernel(const TraceArgs A) {
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
     constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD);
-    using TS = typename TileShape<D>::template S<trace_big_tile(MODE, NS)>;
-    extern __shared__ float smem[];
+    using TS = TileShape<D>;
     const VT* V = static_cast<const VT*>(A.V);
     const VT* dV = static_cast<const VT*>(A.dV);
 
@@ -505,39 +542,15 @@ __global__ void __launch_bounds__(trace_big_tile(MODE, NS) ? 512 : 256,
     const int by = b % A.tiles[1];
     const int bz = b / A.tiles[1];
     const int t = threadIdx.x;
-    const int v0[3] = {bx * TS::X, by * TS::Y, bz * TS::Z};
     int idx[3];
-    idx[0] = v0[0] + t % TS::X;
-    idx[1] = v0[1] + (t / TS::X) % TS::Y;
-    idx[2] = v0[2] + t / (TS::X * TS::Y);
+    idx[0] = bx * TS::X + t % TS::X;
+    idx[1] = by * TS::Y + (t / TS::X) % TS::Y;
+    idx[2] = bz * TS::Z + t / (TS::X * TS::Y);
     const bool active = idx[0] < A.ig.m[0] && idx[1] < A.ig.m[1] && (D == 2 || idx[2] < A.ig.m[2]);
     double ssd = 0.0;
 
     Scatter<D> S;
     S.G = static_cast<VT*>(A.G);
-    S.sm = nullptr;
-    S.n = 0;
-    if (ADJOINT && !NS && A.sm_bytes > 0) {
-        // tile of padded velocity nodes covering this CTA's start cells plus the halo
-        const int ext[3] = {TS::X, TS::Y, TS::Z};
-        int n = 1;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const double xlo = A.vxi_a[a] + ((double)v0[a] + 0.5) * A.vxi_b[a];
-            int lo = (int)floor(xlo) - LGNK_HALO + LGNK_PAD;
-            lo = max(lo, 0);
-            lo = min(lo, A.vg.mp[a] - 1);
-            const int E = min(A.smE[a], A.vg.mp[a] - lo);
-            S.o[a] = lo;
-            S.E[a] = E;
-            n *= E;
-            (void)ext;
-        }
-        S.n = n;
-        S.sm = smem;
-        for (int i = t; i < n * D; i += blockDim.x) smem[i] = 0.0f;
-        __syncthreads();
-    }
 
     if (active) {
         const int vox = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
@@ -551,6 +564,7 @@ __global__ void __launch_bounds__(trace_big_tile(MODE, NS) ? 512 : 256,
         }
         float hist[ADJOINT ? LGNK_MAX_STEPS : 1][D];
 
+#pragma unroll 1
         for (int k = 0; k < A.N; ++k) {
             const float tk = A.t0 + (float)k * A.dt;
             if (ADJOINT) {
@@ -624,30 +638,11 @@ __global__ void __launch_bounds__(trace_big_tile(MODE, NS) ? 512 : 256,
         }
 
         if (ADJOINT) {
+#pragma unroll 1
             for (int k = A.N - 1; k >= 0; --k) {
                 const float tk = A.t0 + (float)k * A.dt;
                 rk4_adjoint_step<D, NS>(A, sv, V, S, hist[ADJOINT ? k : 0], lam, tk);
             }
-        }
-    }
-
-    if (ADJOINT && S.sm != nullptr) {
-        // flush the tile: one vector atomic per touched node (stationary: K = 1)
-        __syncthreads();
-        for (int i = t; i < S.n; i += blockDim.x) {
-            float val[D];
-            bool nz = false;
-#pragma unroll
-            for (int q = 0; q < D; ++q) {
-                val[q] = S.sm[q * S.n + i];
-                nz = nz || val[q] != 0.0f;
-            }
-            if (!nz) continue;
-            int pp[3];
-            pp[0] = S.o[0] + i % S.E[0];
-            pp[1] = S.o[1] + (i / S.E[0]) % S.E[1];
-            pp[2] = (D == 3) ? S.o[2] + i / (S.E[0] * S.E[1]) : 0;
-            red_vec(S.G + linear<D>(A.vg, pp), val, 1.0f);
         }
     }
 
@@ -664,24 +659,11 @@ static cudaError_t launch_one(const TraceArgs& a0, int nblocks, cudaStream_t s) 
     (void)nblocks;
     TraceArgs a = a0;
     int ts[3];
-    trace_tile_shape(D, MODE, NS, ts);
+    trace_tile_shape(D, ts);
     for (int i = 0; i < 3; ++i) a.tiles[i] = (a.ig.m[i] + ts[i] - 1) / ts[i];
     const int blocks = a.tiles[0] * a.tiles[1] * a.tiles[2];
     const int threads = ts[0] * ts[1] * ts[2];
-    size_t smem = 0;
-    if (trace_mode_adjoint(MODE) && !NS && a.sm_bytes > 0) {
-        smem = (size_t)a.sm_bytes;
-        static bool attr_set = false;
-        if (!attr_set && smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(trace_kernel<D, NS, MODEL, MODE>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, LGNK_TILE_SMEM_MAX);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
-    } else {
-        a.sm_bytes = 0;
-    }
-    trace_kernel<D, NS, MODEL, MODE><<<blocks, threads, smem, s>>>(a);
+    trace_kernel<D, NS, MODEL, MODE><<<blocks, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
