@@ -179,9 +179,13 @@ TraceArgs base_args(const lgnk_ctx* ctx) {
             const double hi = (gi.hi[i] - gi.lo[i]) / gi.m[i], hv = (gv.hi[i] - gv.lo[i]) / gv.m[i];
             a.vxi_a[i] = (gi.lo[i] - gv.lo[i]) / hv - 0.5;
             a.vxi_b[i] = hi / hv;
+            a.vxi_af[i] = (float)a.vxi_a[i];
+            a.vxi_bf[i] = (float)a.vxi_b[i];
         } else {
             a.vxi_a[i] = 0.0;
             a.vxi_b[i] = 0.0;
+            a.vxi_af[i] = 0.0f;
+            a.vxi_bf[i] = 0.0f;
         }
     }
     a.V = ctx->Vp;

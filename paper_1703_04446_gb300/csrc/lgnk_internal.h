@@ -42,6 +42,7 @@ struct TraceArgs {
     // continuous velocity-grid index of the start point of voxel i along axis a:
     // vxi_a[a] + (i + 1/2) * vxi_b[a]  (exact in FP64: (x_c - lo_v) / h_v - 1/2)
     double vxi_a[3], vxi_b[3];
+    float vxi_af[3], vxi_bf[3];  // the same in FP32 (per-stage recomputation)
     const void* V;            // packed velocity, [zp][yp][xp][K] of float4 (3D) / float2 (2D)
     const void* dV;           // packed direction (JVP, HESS)
     const float* Tp;          // padded template (gathers)

@@ -33,7 +33,7 @@
 //
 // Gradient scatter.  (d_v I)^T mu goes to the padded gradient accumulator with
 // one vector reduction (red.global.add.v4.f32 / .v2) per corner, executed by
-// the L2 atomic units.  A shared-memory tile of the velocity grid was measured
+// the L2 atomic units; consecutive stages in the same cell are combined first.  A shared-memory tile of the velocity grid was measured
 // slower: float atomics on shared memory retry under the heavy same-address
 // contention of neighbouring characteristics.
 #pragma once
@@ -79,15 +79,39 @@ __device__ __forceinline__ void start_on_image(const int* idx, Start<D>& s) {
     }
 }
 
+template <int D> struct TileShape;
+template <> struct TileShape<2> { static constexpr int X = 16, Y = 16, Z = 1; };
+template <> struct TileShape<3> { static constexpr int X = 8, Y = 8, Z = 4; };
+
+// Voxel handled by this thread (recomputed from the block and thread indices
+// where needed rather than held in registers).
 template <int D>
-__device__ __forceinline__ void start_on_velocity(const TraceArgs& A, const int* idx, Start<D>& s) {
+__device__ __forceinline__ void voxel_index(const TraceArgs& A, int* idx) {
+    using TS = TileShape<D>;
+    int b = blockIdx.x;
+    const int bx = b % A.tiles[0];
+    b /= A.tiles[0];
+    const int by = b % A.tiles[1];
+    const int bz = b / A.tiles[1];
+    const int t = threadIdx.x;
+    idx[0] = bx * TS::X + t % TS::X;
+    idx[1] = by * TS::Y + (t / TS::X) % TS::Y;
+    idx[2] = bz * TS::Z + t / (TS::X * TS::Y);
+}
+
+// Start of this thread's characteristic on the velocity grid:
+// (x_c - lo_v) / h_v - 1/2 = vxi_a + (i + 1/2) vxi_b, evaluated in FP32 (one
+// rounding, below 1e-5 cells for grids up to 2^7 cells).
+template <int D>
+__device__ __forceinline__ void start_on_velocity(const TraceArgs& A, Start<D>& s) {
+    int idx[3];
+    voxel_index<D>(A, idx);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const double xi = A.vxi_a[a] + ((double)idx[a] + 0.5) * A.vxi_b[a];
-        const double fl = floor(xi);
-        const int i0 = (int)fmax(fmin(fl, (double)A.vg.m[a]), -2.0);
+        const float xi = fmaf((float)idx[a] + 0.5f, A.vxi_bf[a], A.vxi_af[a]);
+        const int i0 = min(max((int)floorf(xi), -2), A.vg.m[a]);
         s.I0[a] = i0;
-        s.F0[a] = (float)(xi - (double)i0);
+        s.F0[a] = xi - (float)i0;
     }
 }
 
@@ -165,11 +189,11 @@ __device__ __forceinline__ void corner_value(const typename VecT<D>::type* __res
 __device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
 
 // Element index of corner (cx, cy, cz) of the cell with lower corner `base`.
-template <int D>
+template <int D, bool NS>
 __device__ __forceinline__ size_t corner_elem(const DevGrid& g, int base, int cx, int cy, int cz, int K, int jt) {
     int o = base + cx + cy * g.mp[0];
     if (D == 3) o += cz * g.mp[0] * g.mp[1];
-    return (size_t)o * K + jt;
+    return NS ? (size_t)o * K + jt : (size_t)o;   // stationary: K = 1
 }
 
 // One plane (fixed z corner) of the cell: bilinear value and the unscaled
@@ -178,10 +202,10 @@ template <int D, bool NS, bool GRAD>
 __device__ __forceinline__ void plane(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V, int base,
                                       int cz, int jt, float th, const float* f, float* val, float* dx, float* dy) {
     float c00[D], c10[D], c01[D], c11[D];
-    corner_value<D, NS>(V, corner_elem<D>(g, base, 0, 0, cz, K, jt), th, c00);
-    corner_value<D, NS>(V, corner_elem<D>(g, base, 1, 0, cz, K, jt), th, c10);
-    corner_value<D, NS>(V, corner_elem<D>(g, base, 0, 1, cz, K, jt), th, c01);
-    corner_value<D, NS>(V, corner_elem<D>(g, base, 1, 1, cz, K, jt), th, c11);
+    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 0, cz, K, jt), th, c00);
+    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 1, 0, cz, K, jt), th, c10);
+    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 1, cz, K, jt), th, c01);
+    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 1, 1, cz, K, jt), th, c11);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
         const float a0 = lerp(c00[q], c10[q], f[0]);
@@ -203,7 +227,7 @@ __device__ __forceinline__ void plane_dot(const DevGrid& g, int K, const typenam
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float a[D];
-        corner_value<D, NS>(V, corner_elem<D>(g, base, k & 1, k >> 1, cz, K, jt), th, a);
+        corner_value<D, NS>(V, corner_elem<D, NS>(g, base, k & 1, k >> 1, cz, K, jt), th, a);
         float s = 0.0f;
 #pragma unroll
         for (int q = 0; q < D; ++q) s = fmaf(a[q], mu[q], s);
@@ -262,17 +286,75 @@ __device__ __forceinline__ void stage_tangent(const DevGrid& g, int K, const typ
     stage_value<D, NS>(g, K, dV, p, f, jt, th, dval);
 }
 
-// Destination of the adjoint scatter (d_v I)^T mu: the padded gradient accumulator.
+// Destination of the adjoint scatter (d_v I)^T mu: the padded gradient
+// accumulator, with a one-entry write-combining slot.  Consecutive adjoint
+// stages of a characteristic usually fall in the same velocity cell (and time
+// slot); their contributions w_c(f) mu are then summed per corner and sent as
+// one vector reduction instead of two.
 template <int D>
 struct Scatter {
     typename VecT<D>::type* G;
+    int base;       // cell of the pending contribution, -1 if none
+    int jt;
+    float th;
+    float f[D];
+    float mu[D];
 };
+
+template <int D, bool NS>
+__device__ __forceinline__ void scatter_flush(const DevGrid& g, int K, Scatter<D>& S, bool two, const float* f2,
+                                              const float* mu2, float th2) {
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        float w = (c & 1 ? S.f[0] : 1.0f - S.f[0]) * ((c >> 1) & 1 ? S.f[1] : 1.0f - S.f[1]);
+        if (D == 3) w *= ((c >> 2) & 1) ? S.f[D - 1] : 1.0f - S.f[D - 1];
+        float w2 = 0.0f;
+        if (two) {
+            w2 = (c & 1 ? f2[0] : 1.0f - f2[0]) * ((c >> 1) & 1 ? f2[1] : 1.0f - f2[1]);
+            if (D == 3) w2 *= ((c >> 2) & 1) ? f2[D - 1] : 1.0f - f2[D - 1];
+        }
+        const size_t e = corner_elem<D, NS>(g, S.base, c & 1, (c >> 1) & 1, (c >> 2) & 1, K, S.jt);
+        float x[D];
+        if (NS) {
+#pragma unroll
+            for (int q = 0; q < D; ++q) x[q] = w * (1.0f - S.th) * S.mu[q] + w2 * (1.0f - th2) * mu2[q];
+            red_vec(S.G + e, x, 1.0f);
+#pragma unroll
+            for (int q = 0; q < D; ++q) x[q] = w * S.th * S.mu[q] + w2 * th2 * mu2[q];
+            red_vec(S.G + e + 1, x, 1.0f);
+        } else {
+#pragma unroll
+            for (int q = 0; q < D; ++q) x[q] = fmaf(w2, mu2[q], w * S.mu[q]);
+            red_vec(S.G + e, x, 1.0f);
+        }
+    }
+    S.base = -1;
+}
+
+// Add the contribution w_c(f) mu at cell `base`, time slot (jt, th).
+template <int D, bool NS>
+__device__ __forceinline__ void scatter_add(const DevGrid& g, int K, Scatter<D>& S, int base, const float* f,
+                                            int jt, float th, const float* mu) {
+    if (S.base == base && S.jt == jt) {
+        scatter_flush<D, NS>(g, K, S, true, f, mu, th);
+        return;
+    }
+    if (S.base >= 0) scatter_flush<D, NS>(g, K, S, false, f, mu, th);
+    S.base = base;
+    S.jt = jt;
+    S.th = th;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        S.f[a] = f[a];
+        S.mu[a] = mu[a];
+    }
+}
 
 // Adjoint stage: scatter w_c * (time weight) * mu into the gradient and return
 // nu = d_y I(v, y, t)^T mu = grad_y (v . mu) of the interpolant.
 template <int D, bool NS>
 __device__ __forceinline__ void stage_adjoint(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
-                                              const Scatter<D>& S, const int* p, const float* f, int jt, float th,
+                                              Scatter<D>& S, const int* p, const float* f, int jt, float th,
                                               const float* mu, float* nu) {
     const int base = linear<D>(g, p);
     float s0, dx, dy;
@@ -286,21 +368,7 @@ __device__ __forceinline__ void stage_adjoint(const DevGrid& g, int K, const typ
     }
     nu[0] = dx * g.inv_h[0];
     nu[1] = dy * g.inv_h[1];
-    // scatter with the multilinear weights
-    const float wx[2] = {1.0f - f[0], f[0]};
-    const float wy[2] = {1.0f - f[1], f[1]};
-#pragma unroll
-    for (int c = 0; c < (1 << D); ++c) {
-        float w = wx[c & 1] * wy[(c >> 1) & 1];
-        if (D == 3) w *= ((c >> 2) & 1) ? f[D - 1] : 1.0f - f[D - 1];
-        const size_t e = corner_elem<D>(g, base, c & 1, (c >> 1) & 1, (c >> 2) & 1, K, jt);
-        if (NS) {
-            red_vec(S.G + e, mu, w * (1.0f - th));
-            red_vec(S.G + e + 1, mu, w * th);
-        } else {
-            red_vec(S.G + e, mu, w);
-        }
-    }
+    scatter_add<D, NS>(g, K, S, base, f, jt, th, mu);
 }
 
 // T(y) and optionally grad T(y) from the padded image, y at displacement u.
@@ -360,8 +428,14 @@ struct Slots {
     float th1, th2, th4;
 };
 
+template <bool NS>
 __device__ __forceinline__ Slots step_slots(const TraceArgs& A, float tk) {
     Slots s;
+    if (!NS) {
+        s.j1 = s.j2 = s.j4 = 0;
+        s.th1 = s.th2 = s.th4 = 0.0f;
+        return s;
+    }
     time_slot(A.K, tk, s.j1, s.th1);
     time_slot(A.K, tk + 0.5f * A.dt, s.j2, s.th2);
     time_slot(A.K, tk + A.dt, s.j4, s.th4);
@@ -371,9 +445,11 @@ __device__ __forceinline__ Slots step_slots(const TraceArgs& A, float tk) {
 // One RK4 step of the characteristic (Alg. 1 without the derivative), on the
 // displacement u.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_step(const TraceArgs& A, const Start<D>& sv,
-                                         const typename VecT<D>::type* V, float* u, float tk) {
-    const Slots sl = step_slots(A, tk);
+__device__ __forceinline__ void rk4_step(const TraceArgs& A, const typename VecT<D>::type* V, float* u,
+                                         float tk) {
+    const Slots sl = step_slots<NS>(A, tk);
+    Start<D> sv;
+    start_on_velocity<D>(A, sv);
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
     float f[D], vs[D], us[D], acc[D];
@@ -399,11 +475,12 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const Start<D>& sv,
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const Start<D>& sv,
-                                                 const typename VecT<D>::type* V,
+__device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const typename VecT<D>::type* V,
                                                  const typename VecT<D>::type* dV, float* u, float* dy,
                                                  float tk) {
-    const Slots sl = step_slots(A, tk);
+    const Slots sl = step_slots<NS>(A, tk);
+    Start<D> sv;
+    start_on_velocity<D>(A, sv);
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
     float f[D], us[D], q[D], vs[D], Jq[D], dvs[D], sv_acc[D], sd_acc[D], Ds;
@@ -456,10 +533,11 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const Start
 // its start.  Stage positions are recomputed from the step start u; each
 // stage's J^T mu and scatter share one pass over its corners.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const Start<D>& sv,
-                                                 const typename VecT<D>::type* V, const Scatter<D>& S,
-                                                 const float* u, float* lam, float tk) {
-    const Slots sl = step_slots(A, tk);
+__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const typename VecT<D>::type* V,
+                                                 Scatter<D>& S, const float* u, float* lam, float tk) {
+    const Slots sl = step_slots<NS>(A, tk);
+    Start<D> sv;
+    start_on_velocity<D>(A, sv);
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
     float f[D], vs[D], u2[D], u3[D], u4[D];
@@ -519,10 +597,6 @@ __device__ __forceinline__ double block_sum(double x) {
     return s;
 }
 
-template <int D> struct TileShape;
-template <> struct TileShape<2> { static constexpr int X = 16, Y = 16, Z = 1; };
-template <> struct TileShape<3> { static constexpr int X = 8, Y = 8, Z = 4; };
-
 template <int D, bool NS, int MODEL, int MODE>
 // 256 threads; FWD at 64 registers (4 CTAs per SM), the derivative modes at 80
 // (3 CTAs): measured fastest among 64/80/128-register and 256/512-thread
@@ -532,30 +606,20 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
     constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD);
-    using TS = TileShape<D>;
     const VT* V = static_cast<const VT*>(A.V);
     const VT* dV = static_cast<const VT*>(A.dV);
 
-    int b = blockIdx.x;
-    const int bx = b % A.tiles[0];
-    b /= A.tiles[0];
-    const int by = b % A.tiles[1];
-    const int bz = b / A.tiles[1];
-    const int t = threadIdx.x;
     int idx[3];
-    idx[0] = bx * TS::X + t % TS::X;
-    idx[1] = by * TS::Y + (t / TS::X) % TS::Y;
-    idx[2] = bz * TS::Z + t / (TS::X * TS::Y);
+    voxel_index<D>(A, idx);
     const bool active = idx[0] < A.ig.m[0] && idx[1] < A.ig.m[1] && (D == 2 || idx[2] < A.ig.m[2]);
     double ssd = 0.0;
 
     Scatter<D> S;
     S.G = static_cast<VT*>(A.G);
+    S.base = -1;
 
     if (active) {
         const int vox = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
-        Start<D> sv;
-        start_on_velocity<D>(A, idx, sv);
         float u[D], dy[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -571,8 +635,8 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
 #pragma unroll
                 for (int a = 0; a < D; ++a) hist[ADJOINT ? k : 0][a] = u[a];
             }
-            if (TANGENT) rk4_tangent_step<D, NS>(A, sv, V, dV, u, dy, tk);
-            else rk4_step<D, NS>(A, sv, V, u, tk);
+            if (TANGENT) rk4_tangent_step<D, NS>(A, V, dV, u, dy, tk);
+            else rk4_step<D, NS>(A, V, u, tk);
         }
         if (A.yout != nullptr) {
             const int M = A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
@@ -641,8 +705,9 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
 #pragma unroll 1
             for (int k = A.N - 1; k >= 0; --k) {
                 const float tk = A.t0 + (float)k * A.dt;
-                rk4_adjoint_step<D, NS>(A, sv, V, S, hist[ADJOINT ? k : 0], lam, tk);
+                rk4_adjoint_step<D, NS>(A, V, S, hist[ADJOINT ? k : 0], lam, tk);
             }
+            if (S.base >= 0) scatter_flush<D, NS>(A.vg, A.K, S, false, S.f, S.mu, S.th);
         }
     }
 
