@@ -177,6 +177,31 @@ void lgnk_solve_opts_default(lgnk_solve_opts* opts);
 lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v_inout,
                        const lgnk_solve_opts* opts, lgnk_solve_report* report);
 
+/* Allocation-free transport forward and SSD, for callers that must not call
+ * cudaMalloc after start-up: a latency-critical loop (cudaMalloc can
+ * synchronise the device and takes unbounded time) or a process whose device
+ * memory already belongs to another allocator (a framework's caching
+ * allocator, a pool sized at start-up).  The paper has no counterpart; this is
+ * lgnk_forward (plus the SSD of lgnk_objective) for LGNK_TRANSPORT without a
+ * context.
+ *
+ * prob: validated as in lgnk_create; model must be LGNK_TRANSPORT.
+ * v[n], T[M] in; u1[M] out (device).  R[M] (device) and D (device, one double)
+ * are both NULL or both given: D = h^d/2 |u1 - R|^2, summed in FP64.
+ * stream: cudaStream_t (NULL = legacy default stream); the call only enqueues.
+ *
+ * Scratch: a file-scope device array of 16 MiB (every GPU that loads the
+ * library holds it until exit).  A problem whose packed velocity, padded
+ * template and partial sums exceed it is rejected with LGNK_ERR_INVALID_ARG
+ * (the 128^3 image / 64^3 velocity workload fits).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Errors: the status, with detail from
+ * lgnk_last_error(NULL).  Allocates nothing. */
+lgnk_status lgnk_forward_transport_static(const lgnk_problem* prob, const float* v, const float* T,
+                                          const float* R, float* u1, double* D, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -415,6 +415,16 @@ bool distinct(const void* out, std::initializer_list<const void*> ins) {
 
 }  // namespace
 
+// ---- helpers shared with the allocation-free entry point (static_scratch.cu) ----
+
+const char* lgnk_internal_validate(const lgnk_problem* p) { return validate_problem(p); }
+
+DevGrid lgnk_internal_grid(const lgnk_grid& g) { return make_grid(g); }
+
+void lgnk_internal_set_error(const char* msg) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg ? msg : "");
+}
+
 #define CHECK_CTX()                                                  \
     do {                                                             \
         if (ctx == nullptr) return LGNK_ERR_INVALID_ARG;             \

@@ -94,3 +94,8 @@ cudaError_t launch_scale_modes(float* x, const float* inv_eig, size_t block_elem
 cudaError_t launch_axpby(float a, const float* x, float b, float* y, size_t count, cudaStream_t s);
 cudaError_t launch_add_scaled(float* out, const float* x, float ax, const float* y, float ay, size_t count,
                               cudaStream_t s);
+
+// api.cu helpers for entry points that run without a context
+const char* lgnk_internal_validate(const lgnk_problem* p);  // NULL if valid, else why not
+DevGrid lgnk_internal_grid(const lgnk_grid& g);
+void lgnk_internal_set_error(const char* msg);             // read back by lgnk_last_error(NULL)

@@ -80,6 +80,7 @@ EXPORTS = {
     "lgnk_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lgnk_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "lgnk_forward_transport_static": (ctypes.c_int, [ctypes.POINTER(_Problem)] + [ctypes.c_void_p] * 6),
     "lgnk_solve_opts_default": (None, [ctypes.POINTER(_SolveOpts)]),
     "lgnk_solve": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.POINTER(_SolveOpts),
                                                          ctypes.POINTER(_SolveReport)]),
