@@ -1,0 +1,66 @@
+"""lgnk_solve (inexact Gauss-Newton-Krylov with Armijo, Eq. 11) against the
+oracle's Gauss-Newton on the 2D transport workload (GN 10 outer / 20 inner)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lagrangian as L
+from oracle.objective import Problem as OP, objective
+from oracle.solver import gauss_newton
+from paper_1703_04446_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(model="transport", K=1):
+    from paper_1703_04446_gb300 import lgnk
+    ins = synth.make_inputs("2d_transport_64", seed=3)
+    wl = ins["workload"]
+    prob = lgnk.Problem.from_workload(wl, model=model, time_nodes=K, gamma=1e-4)
+    op = OP(L.Grid(wl.image.m), L.Grid(wl.velocity.m), K=K, N=wl.rk4_steps, model=model, reg=wl.regularizer,
+            alpha=wl.alpha, gamma=1e-4)
+    return lgnk, prob, op, ins
+
+
+def test_first_gauss_newton_step_matches_oracle():
+    """From v = 0 both sides take one GN step (PCG 20, tolerance 0.1, Armijo):
+    the objective after it agrees to 1e-4 relative."""
+    lgnk, prob, op, ins = _setup()
+    ctx = lgnk.Context(prob)
+    T, R = (torch.from_numpy(ins[k]).cuda() for k in ("T", "R"))
+    v, rep = ctx.solve(T, R, None, max_gn=1, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=0.0)
+    vo, repo = gauss_newton(op, ins["T"].astype(np.float64), ins["R"].astype(np.float64),
+                            np.zeros(op.vshape), max_gn=1, gtol=0.0, max_pcg=20, pcg_tol=0.1)
+    assert abs(rep["J0"] - repo["J0"]) <= 1e-5 * repo["J0"]
+    assert abs(rep["J"] - repo["J"]) <= 1e-4 * repo["J"]
+    assert rep["gn_iters"] == 1 and rep["pcg_iters"] == repo["pcg_iters"]
+    # the returned v is the iterate whose objective was reported
+    Jv = objective(op, v.cpu().numpy().astype(np.float64), ins["T"].astype(np.float64),
+                   ins["R"].astype(np.float64))[0]
+    assert abs(Jv - rep["J"]) <= 1e-4 * rep["J"]
+
+
+@pytest.mark.parametrize("model,K", [("transport", 1), ("continuity", 2)])
+def test_solve_decreases_objective_like_oracle(model, K):
+    lgnk, prob, op, ins = _setup(model, K)
+    ctx = lgnk.Context(prob)
+    T, R = (torch.from_numpy(ins[k]).cuda() for k in ("T", "R"))
+    v, rep = ctx.solve(T, R, None, max_gn=10, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=1e-3)
+    _, repo = gauss_newton(op, ins["T"].astype(np.float64), ins["R"].astype(np.float64),
+                           np.zeros(op.vshape), max_gn=10, gtol=1e-3, max_pcg=20, pcg_tol=0.1)
+    assert rep["J"] < 0.5 * rep["J0"]
+    assert rep["g"] < rep["g0"]
+    # FP32 and FP64 Gauss-Newton paths may separate slowly; the minimum reached agrees
+    assert abs(rep["J"] - repo["J"]) <= 2e-2 * repo["J0"]
+    assert rep["status_name"] in ("ok", "not converged")
+
+
+def test_nonfinite_input_is_reported():
+    lgnk, prob, op, ins = _setup()
+    ctx = lgnk.Context(prob)
+    T = torch.from_numpy(ins["T"]).cuda()
+    T[3, 4] = float("nan")
+    R = torch.from_numpy(ins["R"]).cuda()
+    with pytest.raises(lgnk.LgnkError) as e:
+        ctx.objective(torch.zeros(prob.velocity_shape, device="cuda"), T, R)
+    assert e.value.status == 4
