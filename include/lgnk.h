@@ -190,7 +190,7 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v_i
  * are both NULL or both given: D = h^d/2 |u1 - R|^2, summed in FP64.
  * stream: cudaStream_t (NULL = legacy default stream); the call only enqueues.
  *
- * Scratch: a file-scope device array of 16 MiB (every GPU that loads the
+ * Scratch: a file-scope device array of 32 MiB (every GPU that loads the
  * library holds it until exit).  A problem whose packed velocity, padded
  * template and partial sums exceed it is rejected with LGNK_ERR_INVALID_ARG
  * (the 128^3 image / 64^3 velocity workload fits).  The first call on a device

@@ -524,9 +524,10 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
         return fail(LGNK_ERR_CUDA);
     }
     const size_t vbytes = ctx->vpad * ctx->K * ctx->vt_bytes;
+    const size_t pbytes = ctx->vpad * ctx->K * velocity_pair_bytes(d);
     lgnk_status s;
-    if ((s = dev_alloc(ctx, vbytes, &ctx->Vp)) != LGNK_OK) return fail(s);
-    if ((s = dev_alloc(ctx, vbytes, &ctx->dVp)) != LGNK_OK) return fail(s);
+    if ((s = dev_alloc(ctx, pbytes, &ctx->Vp)) != LGNK_OK) return fail(s);
+    if ((s = dev_alloc(ctx, pbytes, &ctx->dVp)) != LGNK_OK) return fail(s);
     if ((s = dev_alloc(ctx, vbytes, &ctx->Gp)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, ctx->ipad, &ctx->Tp)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, ctx->ipad, &ctx->acc)) != LGNK_OK) return fail(s);

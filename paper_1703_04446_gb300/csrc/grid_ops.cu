@@ -19,27 +19,38 @@ __device__ __forceinline__ size_t padded_size(const DevGrid& g) {
 
 // ---------------------------------------------------------------- packing --
 
+// Pair-packed velocity: element (node, j) holds the velocity of the padded node
+// and of its +x neighbour at time node j, [v(node) | v(node + 1)], as
+// 8 floats (3D: xyz + zero pad, twice; 32 bytes) or 4 floats (2D).  One
+// 256-bit (3D) or 128-bit (2D) load then returns both x-corners of a cell row.
 template <int D>
 __global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restrict__ Vp, DevGrid g, int K) {
     const size_t total = padded_size(g) * K;
     const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
-    constexpr int W = (D == 3) ? 4 : 2;
+    constexpr int PS = (D == 3) ? 8 : 4;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(i % K);
         const size_t node = i / K;
         const int px = (int)(node % g.mp[0]);
         const int py = (int)((node / g.mp[0]) % g.mp[1]);
         const int pz = (int)(node / ((size_t)g.mp[0] * g.mp[1]));
-        const int x = px - LGNK_PAD, y = py - LGNK_PAD, z = (D == 3) ? pz - LGNK_PAD : 0;
-        const bool in = x >= 0 && x < g.m[0] && y >= 0 && y < g.m[1] && z >= 0 && z < g.m[2];
-        float out[4] = {0.f, 0.f, 0.f, 0.f};
-        if (in) {
-            const size_t s = ((size_t)z * g.m[1] + y) * g.m[0] + x;
+        float out[PS];
 #pragma unroll
-            for (int c = 0; c < D; ++c) out[c] = v[((size_t)j * D + c) * Mv + s];
+        for (int q = 0; q < PS; ++q) out[q] = 0.0f;
+        const int y = py - LGNK_PAD, z = (D == 3) ? pz - LGNK_PAD : 0;
+        const bool yz_in = y >= 0 && y < g.m[1] && z >= 0 && z < g.m[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int x = px + h - LGNK_PAD;
+            if (yz_in && x >= 0 && x < g.m[0]) {
+                const size_t s = ((size_t)z * g.m[1] + y) * g.m[0] + x;
+#pragma unroll
+                for (int c = 0; c < D; ++c) out[h * (PS / 2) + c] = v[((size_t)j * D + c) * Mv + s];
+            }
         }
-        if (W == 4) reinterpret_cast<float4*>(Vp)[i] = make_float4(out[0], out[1], out[2], 0.f);
-        else reinterpret_cast<float2*>(Vp)[i] = make_float2(out[0], out[1]);
+        float4* o = reinterpret_cast<float4*>(Vp + i * PS);
+        o[0] = make_float4(out[0], out[1], out[2], out[3]);
+        if (D == 3) o[1] = make_float4(out[4], out[5], out[6], out[7]);
     }
 }
 

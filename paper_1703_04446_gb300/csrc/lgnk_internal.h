@@ -43,8 +43,8 @@ struct TraceArgs {
     // vxi_a[a] + (i + 1/2) * vxi_b[a]  (exact in FP64: (x_c - lo_v) / h_v - 1/2)
     double vxi_a[3], vxi_b[3];
     float vxi_af[3], vxi_bf[3];  // the same in FP32 (per-stage recomputation)
-    const void* V;            // packed velocity, [zp][yp][xp][K] of float4 (3D) / float2 (2D)
-    const void* dV;           // packed direction (JVP, HESS)
+    const void* V;            // pair-packed velocity [zp][yp][xp][K] x [v(node) | v(node+1)]
+    const void* dV;           // pair-packed direction (JVP, HESS)
     const float* Tp;          // padded template (gathers)
     const float* T;           // template, ABI layout (continuity particle masses)
     const float* R;           // reference, ABI layout (OBJGRAD, FWD with residual)
@@ -52,7 +52,7 @@ struct TraceArgs {
     float* u1;                // transport FWD output (ABI layout)
     float* yout;              // optional end points [d][M]
     float* acc;               // continuity splat accumulator (padded image)
-    void* G;                  // packed gradient accumulator (JTVP, HESS, OBJGRAD)
+    void* G;                  // gradient accumulator [zp][yp][xp][K] of float4 (3D) / float2 (2D)
     double* partial;          // per-block FP64 partial sums of res^2
 };
 
@@ -61,7 +61,9 @@ cudaError_t launch_trace(int d, bool nonstat, int model, int mode, const TraceAr
                          cudaStream_t s);
 
 // grid utilities (grid_ops.cu)
+// ABI velocity -> pair-packed padded layout (pair_bytes(d) bytes per node and time node)
 cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, cudaStream_t s);
+inline size_t velocity_pair_bytes(int d) { return d == 3 ? 32 : 16; }
 cudaError_t launch_unpack_velocity(int d, const void* Gp, float* out, const DevGrid& g, int K,
                                    float scale, cudaStream_t s);
 cudaError_t launch_pack_image(const float* T, float* Tp, const DevGrid& g, int d, float scale, cudaStream_t s);

@@ -14,7 +14,7 @@
 
 // Largest scratch a call may use.  Every GPU that loads the library holds this
 // array until the process exits.
-#define LGNK_STATIC_SCRATCH_BYTES (16u << 20)
+#define LGNK_STATIC_SCRATCH_BYTES (32u << 20)
 
 static __device__ __align__(256) unsigned char g_static_scratch[LGNK_STATIC_SCRATCH_BYTES];
 
@@ -85,7 +85,7 @@ extern "C" lgnk_status lgnk_forward_transport_static(const lgnk_problem* prob, c
         tiles[i] = (ig.m[i] + ts[i] - 1) / ts[i];
         nblocks *= tiles[i];
     }
-    const size_t vbytes = align256((size_t)vg.mp[0] * vg.mp[1] * vg.mp[2] * K * (d == 3 ? 16 : 8));
+    const size_t vbytes = align256((size_t)vg.mp[0] * vg.mp[1] * vg.mp[2] * K * velocity_pair_bytes(d));
     const size_t tbytes = align256((size_t)ig.mp[0] * ig.mp[1] * ig.mp[2] * sizeof(float));
     const size_t pbytes = align256((size_t)nblocks * sizeof(double));
     const size_t need = vbytes + tbytes + pbytes + 256;

@@ -174,15 +174,36 @@ __device__ __forceinline__ void time_slot(int K, float t, int& j, float& th) {
     th = s - (float)jj;
 }
 
+// Both x-corners of a cell row from the pair-packed velocity: element e holds
+// [v(node) | v(node + 1)] (3D: 32 bytes, one 256-bit load; 2D: 16 bytes).
+__device__ __forceinline__ void load_pair3(const float* p, float* a, float* b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, _, %3, %4, %5, _}, [%6];"
+        : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(b[0]), "=f"(b[1]), "=f"(b[2])
+        : "l"(p));
+}
+
 template <int D, bool NS>
-__device__ __forceinline__ void corner_value(const typename VecT<D>::type* __restrict__ V, size_t e, float th,
-                                             float* a) {
-    load_vec(V + e, a);
+__device__ __forceinline__ void pair_value(const float* __restrict__ V, size_t e, float th, float* a, float* b) {
+    constexpr int PS = (D == 3) ? 8 : 4;
+    if (D == 3) {
+        load_pair3(V + e * PS, a, b);
+    } else {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(V + e * PS));
+        a[0] = t.x; a[1] = t.y; b[0] = t.z; b[1] = t.w;
+    }
     if (NS) {
-        float b[D];
-        load_vec(V + e + 1, b);
+        float a1[3], b1[3];
+        if (D == 3) {
+            load_pair3(V + (e + 1) * PS, a1, b1);
+        } else {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(V + (e + 1) * PS));
+            a1[0] = t.x; a1[1] = t.y; b1[0] = t.z; b1[1] = t.w;
+        }
 #pragma unroll
-        for (int q = 0; q < D; ++q) a[q] = fmaf(th, b[q] - a[q], a[q]);
+        for (int q = 0; q < D; ++q) {
+            a[q] = fmaf(th, a1[q] - a[q], a[q]);
+            b[q] = fmaf(th, b1[q] - b[q], b[q]);
+        }
     }
 }
 
@@ -199,13 +220,11 @@ __device__ __forceinline__ size_t corner_elem(const DevGrid& g, int base, int cx
 // One plane (fixed z corner) of the cell: bilinear value and the unscaled
 // derivatives along the fractional x and y offsets, per component.
 template <int D, bool NS, bool GRAD>
-__device__ __forceinline__ void plane(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V, int base,
-                                      int cz, int jt, float th, const float* f, float* val, float* dx, float* dy) {
-    float c00[D], c10[D], c01[D], c11[D];
-    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 0, cz, K, jt), th, c00);
-    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 1, 0, cz, K, jt), th, c10);
-    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 1, cz, K, jt), th, c01);
-    corner_value<D, NS>(V, corner_elem<D, NS>(g, base, 1, 1, cz, K, jt), th, c11);
+__device__ __forceinline__ void plane(const DevGrid& g, int K, const float* __restrict__ V, int base, int cz, int jt,
+                                      float th, const float* f, float* val, float* dx, float* dy) {
+    float c00[3], c10[3], c01[3], c11[3];
+    pair_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 0, cz, K, jt), th, c00, c10);
+    pair_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 1, cz, K, jt), th, c01, c11);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
         const float a0 = lerp(c00[q], c10[q], f[0]);
@@ -220,18 +239,22 @@ __device__ __forceinline__ void plane(const DevGrid& g, int K, const typename Ve
 
 // Scalar version: corner values contracted with mu first (s_c = v_c . mu).
 template <int D, bool NS>
-__device__ __forceinline__ void plane_dot(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
-                                          int base, int cz, int jt, float th, const float* f, const float* mu,
-                                          float& val, float& dx, float& dy) {
+__device__ __forceinline__ void plane_dot(const DevGrid& g, int K, const float* __restrict__ V, int base, int cz,
+                                          int jt, float th, const float* f, const float* mu, float& val, float& dx,
+                                          float& dy) {
     float c[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        float a[D];
-        corner_value<D, NS>(V, corner_elem<D, NS>(g, base, k & 1, k >> 1, cz, K, jt), th, a);
-        float s = 0.0f;
+    for (int r = 0; r < 2; ++r) {
+        float a[3], b[3];
+        pair_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, r, cz, K, jt), th, a, b);
+        float sa = 0.0f, sb = 0.0f;
 #pragma unroll
-        for (int q = 0; q < D; ++q) s = fmaf(a[q], mu[q], s);
-        c[k] = s;
+        for (int q = 0; q < D; ++q) {
+            sa = fmaf(a[q], mu[q], sa);
+            sb = fmaf(b[q], mu[q], sb);
+        }
+        c[2 * r] = sa;
+        c[2 * r + 1] = sb;
     }
     const float a0 = lerp(c[0], c[1], f[0]);
     const float a1 = lerp(c[2], c[3], f[0]);
@@ -242,8 +265,8 @@ __device__ __forceinline__ void plane_dot(const DevGrid& g, int K, const typenam
 
 // val = I(v, y, t) (Sec. 3.1, Step 1: multilinear in space, linear in time).
 template <int D, bool NS>
-__device__ __forceinline__ void stage_value(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
-                                            const int* p, const float* f, int jt, float th, float* val) {
+__device__ __forceinline__ void stage_value(const DevGrid& g, int K, const float* __restrict__ V, const int* p, const float* f,
+                                            int jt, float th, float* val) {
     const int base = linear<D>(g, p);
     plane<D, NS, false>(g, K, V, base, 0, jt, th, f, val, nullptr, nullptr);
     if (D == 3) {
@@ -256,8 +279,8 @@ __device__ __forceinline__ void stage_value(const DevGrid& g, int K, const typen
 
 // Tangent stage: val = I(v, y, t), Jq = d_y I(v, y, t) q, dval = I(dv, y, t).
 template <int D, bool NS>
-__device__ __forceinline__ void stage_tangent(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
-                                              const typename VecT<D>::type* __restrict__ dV, const int* p,
+__device__ __forceinline__ void stage_tangent(const DevGrid& g, int K, const float* __restrict__ V,
+                                              const float* __restrict__ dV, const int* p,
                                               const float* f, int jt, float th, const float* qv, float* val,
                                               float* Jq, float* dval) {
     const int base = linear<D>(g, p);
@@ -353,7 +376,7 @@ __device__ __forceinline__ void scatter_add(const DevGrid& g, int K, Scatter<D>&
 // Adjoint stage: scatter w_c * (time weight) * mu into the gradient and return
 // nu = d_y I(v, y, t)^T mu = grad_y (v . mu) of the interpolant.
 template <int D, bool NS>
-__device__ __forceinline__ void stage_adjoint(const DevGrid& g, int K, const typename VecT<D>::type* __restrict__ V,
+__device__ __forceinline__ void stage_adjoint(const DevGrid& g, int K, const float* __restrict__ V,
                                               Scatter<D>& S, const int* p, const float* f, int jt, float th,
                                               const float* mu, float* nu) {
     const int base = linear<D>(g, p);
@@ -445,7 +468,7 @@ __device__ __forceinline__ Slots step_slots(const TraceArgs& A, float tk) {
 // One RK4 step of the characteristic (Alg. 1 without the derivative), on the
 // displacement u.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_step(const TraceArgs& A, const typename VecT<D>::type* V, float* u,
+__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u,
                                          float tk) {
     const Slots sl = step_slots<NS>(A, tk);
     Start<D> sv;
@@ -475,8 +498,8 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const typename VecT
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const typename VecT<D>::type* V,
-                                                 const typename VecT<D>::type* dV, float* u, float* dy,
+__device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float* V, const float* dV, float* u,
+                                                 float* dy,
                                                  float tk) {
     const Slots sl = step_slots<NS>(A, tk);
     Start<D> sv;
@@ -533,7 +556,7 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const typen
 // its start.  Stage positions are recomputed from the step start u; each
 // stage's J^T mu and scatter share one pass over its corners.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const typename VecT<D>::type* V,
+__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V,
                                                  Scatter<D>& S, const float* u, float* lam, float tk) {
     const Slots sl = step_slots<NS>(A, tk);
     Start<D> sv;
@@ -606,8 +629,8 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
     constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD);
-    const VT* V = static_cast<const VT*>(A.V);
-    const VT* dV = static_cast<const VT*>(A.dV);
+    const float* V = static_cast<const float*>(A.V);
+    const float* dV = static_cast<const float*>(A.dV);
 
     int idx[3];
     voxel_index<D>(A, idx);

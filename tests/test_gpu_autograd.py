@@ -24,29 +24,59 @@ def _crop_problem(seed=0):
     return prob, g, vg, T, R, v
 
 
-def test_backward_matches_central_differences():
+def _smooth_crop():
+    """A 16^3 crop with smooth data (two Gaussian blobs, no noise).  On the noisy
+    phantom, a step of h = 1e-3 carries a fifth of the characteristics across
+    kinks of the piecewise-linear interpolants and central differences stop
+    measuring the derivative."""
     from paper_1703_04446_gb300 import lgnk
-    prob, g, vg, T, R, v = _crop_problem()
+    gs = synth.GridSpec((16, 16, 16), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    vs = synth.GridSpec((8, 8, 8), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    c = synth.centres(gs)
+    blobs = [(1.0, 0.15, (0.5, 0.5, 0.5)), (0.6, 0.1, (0.4, 0.6, 0.55))]
+    T = synth.gaussian_blobs(c, blobs).astype(np.float32)
+    R = synth.gaussian_blobs([x - 0.03 for x in c], blobs).astype(np.float32)
+    v = synth.random_velocity(vs, 1, 3.0 / 16, 3).astype(np.float32)
+    prob = lgnk.Problem(image_m=(16, 16, 16), velocity_m=(8, 8, 8), time_nodes=1, rk4_steps=8, alpha=1e-3)
+    return prob, T, R, v
+
+
+def test_backward_matches_central_differences():
+    """Directional derivative of 1/2 |u1(v) - R|^2 from the backward kernel against
+    central differences with h = 1e-3: the GPU's differences equal the oracle's
+    (same kinks) to 1e-3, and the analytic value is within the 1e-2 that kink
+    crossings leave at this h (measured 4e-3 on the oracle alone)."""
+    from paper_1703_04446_gb300 import lgnk
+    prob, T, R, v = _smooth_crop()
     ctx = lgnk.Context(prob)
     tT, tR = torch.from_numpy(T).cuda(), torch.from_numpy(R).cuda()
     tv = torch.from_numpy(v).cuda().requires_grad_(True)
+    ig, og = L.Grid((16, 16, 16)), L.Grid((8, 8, 8))
+    T64, R64 = T.astype(np.float64), R.astype(np.float64)
 
     def loss(vv):
         u1 = lgnk.lagrangian_forward(ctx, vv, tT)
-        return 0.5 * ((u1 - tR) ** 2).sum()
+        return 0.5 * ((u1.double() - tR.double()) ** 2).sum()
 
-    lo = loss(tv)
-    lo.backward()
+    def oracle_loss(vv):
+        u1, _ = L.final_state("transport", vv, og, T64, ig, 8)
+        return 0.5 * float(np.sum((u1 - R64) ** 2))
+
+    loss(tv).backward()
     grad = tv.grad.detach().double()
     rng = np.random.default_rng(7)
     h = 1e-3
     for _ in range(3):
-        d = torch.from_numpy(rng.normal(size=v.shape).astype(np.float32)).cuda()
-        d = d / d.norm() * float(tv.detach().norm())
+        d = rng.normal(size=v.shape)
+        d = (d / np.abs(d).max() * np.abs(v).max()).astype(np.float32)
+        td = torch.from_numpy(d).cuda()
         with torch.no_grad():
-            fd = (loss(tv.detach() + h * d).double() - loss(tv.detach() - h * d).double()) / (2 * h)
-        an = float((grad * d.double()).sum())
-        assert abs(an - float(fd)) <= 2e-3 * max(abs(an), abs(float(fd))), (an, float(fd))
+            fd = float(loss(tv.detach() + h * td) - loss(tv.detach() - h * td)) / (2 * h)
+        v64, d64 = v.astype(np.float64), d.astype(np.float64)
+        fd_o = (oracle_loss(v64 + h * d64) - oracle_loss(v64 - h * d64)) / (2 * h)
+        an = float((grad * td.double()).sum())
+        assert abs(fd - fd_o) <= 1e-3 * abs(fd_o), (fd, fd_o)
+        assert abs(an - fd_o) <= 1e-2 * abs(an), (an, fd_o)
 
 
 def test_backward_matches_oracle_jtvp():

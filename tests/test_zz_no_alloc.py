@@ -2,7 +2,7 @@
 
 It serves callers that must not call cudaMalloc after start-up, such as a
 latency-critical loop or a process whose device memory already belongs to
-another allocator.  Its scratch is a fixed 16 MiB device array shared by all
+another allocator.  Its scratch is a fixed 32 MiB device array shared by all
 calls.  Here it is called twice in a row through the C ABI on different
 problems, and each result is compared with the context-based lgnk_forward and
 the SSD of lgnk_objective.  The file sorts last, so a failure here does not
