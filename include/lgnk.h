@@ -122,9 +122,10 @@ lgnk_status lgnk_objective(lgnk_ctx* ctx, const float* v, const float* T, const 
  * Hdv[n] out. */
 lgnk_status lgnk_hessvec(lgnk_ctx* ctx, const float* v, const float* T, const float* dv, float* Hdv);
 
-/* Spectral preconditioner (Sec. 3.2): z = (alpha dt h_v^d A + gamma I)^+ r through
- * the DCT-II eigenbasis of the Neumann operator A (zero eigenvalues act as 1;
- * elastic uses its mu-Laplacian part).  r[n] in; z[n] out. */
+/* Spectral preconditioner (Sec. 3.2): z = P^-1 r with P = alpha dt h_v^d A + gamma I
+ * applied through the DCT-II eigenbasis of the Neumann operator A; a zero
+ * eigenvalue (gamma = 0, constant mode) takes the smallest nonzero one, keeping
+ * P positive definite (elastic uses its mu-Laplacian part).  r[n] in; z[n] out. */
 lgnk_status lgnk_precond(lgnk_ctx* ctx, const float* r, float* z);
 
 /* FP64 inner product of two device float arrays of length count; host result.

@@ -5,10 +5,11 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 Readings of the paper taken here:
 * The preconditioner is the regularizer's Hessian plus gamma, P = alpha dt h^d A +
-  gamma I, applied through its DCT-II eigen-decomposition; a zero eigenvalue
-  (gamma = 0, constant mode) is replaced by 1, i.e. the pseudo-inverse plus
-  the identity on the null space.  For the elastic model only its mu-Laplacian
-  part is used.
+  gamma I, applied through its DCT-II eigen-decomposition (Sec. 3.2: its
+  pseudo-inverse via the DCT).  A zero eigenvalue (gamma = 0, the constant
+  mode) is replaced by the smallest nonzero one, so P stays positive definite
+  and scales its null space like the rest of its spectrum.  For the elastic
+  model only its mu-Laplacian part is used.
 * Stopping and line-search constants are the textbook ones (the paper defers
   to FAIR's defaults): PCG stops at relative residual 0.1 or 50 iterations
   (Sec. 4.1); Armijo starts at mu = 1, halves, c = 1e-4, at most 10 trials;
@@ -38,14 +39,16 @@ def laplacian_eigenvalues(prob: Problem) -> np.ndarray:
 
 def preconditioner_eigenvalues(prob: Problem) -> np.ndarray:
     """Diagonal of P = alpha dt h^d A_reg + gamma I in the DCT-II basis, with zeros
-    replaced by 1."""
+    replaced by the smallest nonzero entry (1 if all are zero)."""
     lam = laplacian_eigenvalues(prob)
     if prob.reg == "curvature":
         lam = lam * lam
     elif prob.reg == "elastic":
         lam = prob.mu * lam
     p = prob.alpha * prob.time_weight * prob.vgrid.cell_volume * lam + prob.gamma
-    return np.where(p == 0.0, 1.0, p)
+    pos = p[p > 0.0]
+    fill = pos.min() if pos.size else 1.0
+    return np.where(p == 0.0, fill, p)
 
 
 def apply_preconditioner(prob: Problem, r: np.ndarray) -> np.ndarray:

@@ -551,7 +551,7 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     }
 
     // Spectral preconditioner tables (Sec. 3.2): orthonormal DCT-II per axis and
-    // the inverse eigenvalues of alpha dt h_v^d A_reg + gamma I (zero -> 1).
+    // the inverse eigenvalues of alpha dt h_v^d A_reg + gamma I.
     std::vector<float> hostC;
     for (int a = 0; a < d; ++a) {
         const int m = ctx->vg.m[a];
@@ -563,8 +563,9 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
         if (cudaMemcpy(ctx->Cm[a], hostC.data(), hostC.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(LGNK_ERR_CUDA);
     }
-    std::vector<float> ev(ctx->Mv);
+    std::vector<double> pv(ctx->Mv);
     const double wa = prob->alpha * ctx->wreg;
+    double pmin = 0.0;
     for (size_t sidx = 0; sidx < ctx->Mv; ++sidx) {
         size_t r = sidx;
         double lam = 0.0;
@@ -577,8 +578,14 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
         }
         if (prob->regularizer == LGNK_CURVATURE) lam = lam * lam;
         if (prob->regularizer == LGNK_ELASTIC) lam = prob->mu_lame * lam;
-        const double p = wa * lam + prob->gamma;
-        ev[sidx] = (float)(p == 0.0 ? 1.0 : 1.0 / p);
+        pv[sidx] = wa * lam + prob->gamma;
+        if (pv[sidx] > 0.0 && (pmin == 0.0 || pv[sidx] < pmin)) pmin = pv[sidx];
+    }
+    // a zero eigenvalue (gamma = 0: the constant mode) takes the smallest nonzero one
+    std::vector<float> ev(ctx->Mv);
+    for (size_t sidx = 0; sidx < ctx->Mv; ++sidx) {
+        const double p = pv[sidx] > 0.0 ? pv[sidx] : (pmin > 0.0 ? pmin : 1.0);
+        ev[sidx] = (float)(1.0 / p);
     }
     if (cudaMemcpy(ctx->inv_eig, ev.data(), ev.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(LGNK_ERR_CUDA);
