@@ -18,7 +18,7 @@ Workloads (sizes from the paper's experiment classes, Sec. 4.2-4.5):
 * ``2d_continuity_256`` 256^2 unit-mass density of 20 Gaussians, velocity
   128^2 x 2 on 5 time nodes, N = 16, elastic alpha = 1e-3, noise 0.01.
 * ``3d_transport_128``  128^3 nested-ellipsoid phantom, noise 0.01, velocity
-  64^3 x 3, stationary, N = 8, diffusion alpha = 1e-3; reference displaced by
+  64^3 x 3, stationary, N = 8, diffusion alpha = 1e-2; reference displaced by
   up to 8 voxels.
 * ``3d_continuity_brain`` 192 x 224 x 160 shell phantom on
   (0,1.2) x (0,1.4) x (0,1), velocity 96 x 112 x 80 x 3 on 9 time nodes,
@@ -88,7 +88,7 @@ WORKLOADS = {
         "continuity", "elastic", 1e-3, 0.0, {"mu": 1.0, "lam": 0.0}),
     "3d_transport_128": Workload(
         "3d_transport_128", _box((128, 128, 128)), _box((64, 64, 64)), 1, 8,
-        "transport", "diffusion", 1e-3, 0.0),
+        "transport", "diffusion", 1e-2, 0.0),
     "3d_continuity_brain": Workload(
         "3d_continuity_brain", _box((192, 224, 160), hi=(1.2, 1.4, 1.0)),
         _box((96, 112, 80), hi=(1.2, 1.4, 1.0)), 9, 16,
