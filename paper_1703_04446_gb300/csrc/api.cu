@@ -28,7 +28,8 @@ struct lgnk_ctx {
     int d = 0, K = 0, N = 0;
     size_t M = 0, Mv = 0, n = 0;  // image voxels, velocity nodes per block, unknowns
     size_t ipad = 0, vpad = 0;    // padded image elements, padded velocity nodes
-    size_t vt_bytes = 0;          // bytes of one packed velocity element
+    size_t vt_bytes = 0;          // bytes of one gradient-accumulator element
+    SliceTable slices{};          // stage-time slices of the velocity
     int tiles[3] = {1, 1, 1};
     int trace_blocks = 0;
     double cellvol = 0.0;         // image h^d (Eq. 10)
@@ -188,6 +189,7 @@ TraceArgs base_args(const lgnk_ctx* ctx) {
             a.vxi_bf[i] = 0.0f;
         }
     }
+    a.slice_nodes = (long long)ctx->vpad;
     a.V = ctx->Vp;
     a.dV = ctx->dVp;
     a.Tp = ctx->Tp;
@@ -223,7 +225,7 @@ lgnk_status trace(lgnk_ctx* ctx, int mode, const TraceArgs& a) {
 }
 
 lgnk_status pack_v(lgnk_ctx* ctx, const float* v, void* dst) {
-    KL(launch_pack_velocity(ctx->d, v, dst, ctx->vg, ctx->K, ctx->stream));
+    KL(launch_pack_velocity(ctx->d, v, dst, ctx->vg, ctx->K, ctx->slices, ctx->stream));
     return LGNK_OK;
 }
 
@@ -233,7 +235,7 @@ lgnk_status pack_T(lgnk_ctx* ctx, const float* T) {
 }
 
 lgnk_status zero_G(lgnk_ctx* ctx) {
-    CK(cudaMemsetAsync(ctx->Gp, 0, ctx->vpad * ctx->K * ctx->vt_bytes, ctx->stream));
+    CK(cudaMemsetAsync(ctx->Gp, 0, ctx->vpad * ctx->slices.n * ctx->vt_bytes, ctx->stream));
     return LGNK_OK;
 }
 
@@ -344,7 +346,7 @@ lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, cons
     }
     KL(launch_reduce(ctx->partial, nred, ctx->dres + 0, ctx->stream));
     if (grad != nullptr) {
-        KL(launch_unpack_velocity(ctx->d, ctx->Gp, grad, ctx->vg, ctx->K, 1.0f, ctx->stream));
+        KL(launch_distribute_gradient(ctx->d, ctx->Gp, grad, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
         TRY(reg_apply(ctx, v, grad, ctx->prob.alpha * ctx->wreg, 0.0, grad));
     }
     // S = 1/2 dt h_v^d v^T A_reg v
@@ -382,7 +384,7 @@ lgnk_status hessvec_packed(lgnk_ctx* ctx, const float* T, const float* dv, float
         b.r = ctx->acc;
         TRY(trace(ctx, MODE_JTVP, b));
     }
-    KL(launch_unpack_velocity(ctx->d, ctx->Gp, out, ctx->vg, ctx->K, 1.0f, ctx->stream));
+    KL(launch_distribute_gradient(ctx->d, ctx->Gp, out, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
     return reg_apply(ctx, dv, out, ctx->prob.alpha * ctx->wreg, ctx->prob.gamma, out);
 }
 
@@ -523,8 +525,12 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
         cudaGetLastError();
         return fail(LGNK_ERR_CUDA);
     }
-    const size_t vbytes = ctx->vpad * ctx->K * ctx->vt_bytes;
-    const size_t pbytes = ctx->vpad * ctx->K * velocity_pair_bytes(d);
+    {
+        const bool transport = prob->model == LGNK_TRANSPORT;
+        make_slice_table(ctx->K, ctx->N, transport ? 1.0 : 0.0, (transport ? -1.0 : 1.0) / ctx->N, &ctx->slices);
+    }
+    const size_t vbytes = ctx->vpad * ctx->slices.n * ctx->vt_bytes;
+    const size_t pbytes = ctx->vpad * ctx->slices.n * velocity_pair_bytes(d);
     lgnk_status s;
     if ((s = dev_alloc(ctx, pbytes, &ctx->Vp)) != LGNK_OK) return fail(s);
     if ((s = dev_alloc(ctx, pbytes, &ctx->dVp)) != LGNK_OK) return fail(s);
@@ -639,7 +645,7 @@ lgnk_status lgnk_jtvp(lgnk_ctx* ctx, const float* v, const float* T, const float
         a.r = ctx->rp;
     }
     TRY(trace(ctx, MODE_JTVP, a));
-    KL(launch_unpack_velocity(ctx->d, ctx->Gp, gv, ctx->vg, ctx->K, 1.0f, ctx->stream));
+    KL(launch_distribute_gradient(ctx->d, ctx->Gp, gv, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
     return LGNK_OK;
 }
 

@@ -2,6 +2,8 @@
 // and the padded packed layout of the tracing kernels, FP64 reductions,
 // regularizer stencils (Sec. 2.1, Sec. 3.2), the per-axis DCT of the spectral
 // preconditioner (Sec. 3.2) and the vector updates of PCG.
+#include <cmath>
+
 #include "lgnk_internal.h"
 
 namespace {
@@ -19,18 +21,22 @@ __device__ __forceinline__ size_t padded_size(const DevGrid& g) {
 
 // ---------------------------------------------------------------- packing --
 
-// Pair-packed velocity: element (node, j) holds the velocity of the padded node
-// and of its +x neighbour at time node j, [v(node) | v(node + 1)], as
-// 8 floats (3D: xyz + zero pad, twice; 32 bytes) or 4 floats (2D).  One
-// 256-bit (3D) or 128-bit (2D) load then returns both x-corners of a cell row.
+// Pair-packed time slices: element (m, node) holds the velocity at stage time
+// t_m (linear in time between the K nodes) at the padded node and at its +x
+// neighbour, [v(node) | v(node + 1)], as 8 floats (3D: xyz + zero pad, twice;
+// 32 bytes) or 4 floats (2D).  One 256-bit (3D) or 128-bit (2D) load then
+// returns both x-corners of a cell row.
 template <int D>
-__global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restrict__ Vp, DevGrid g, int K) {
-    const size_t total = padded_size(g) * K;
+__global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restrict__ Vp, DevGrid g, SliceTable tab) {
+    const size_t nodes = padded_size(g);
+    const size_t total = nodes * tab.n;
     const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
     constexpr int PS = (D == 3) ? 8 : 4;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(i % K);
-        const size_t node = i / K;
+        const int m = (int)(i / nodes);
+        const size_t node = i % nodes;
+        const int j = tab.j[m];
+        const float th = tab.th[m];
         const int px = (int)(node % g.mp[0]);
         const int py = (int)((node / g.mp[0]) % g.mp[1]);
         const int pz = (int)(node / ((size_t)g.mp[0] * g.mp[1]));
@@ -45,7 +51,12 @@ __global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restr
             if (yz_in && x >= 0 && x < g.m[0]) {
                 const size_t s = ((size_t)z * g.m[1] + y) * g.m[0] + x;
 #pragma unroll
-                for (int c = 0; c < D; ++c) out[h * (PS / 2) + c] = v[((size_t)j * D + c) * Mv + s];
+                for (int c = 0; c < D; ++c) {
+                    const float a = v[((size_t)j * D + c) * Mv + s];
+                    float val = a;
+                    if (th != 0.0f) val = fmaf(th, v[((size_t)(j + 1) * D + c) * Mv + s] - a, a);
+                    out[h * (PS / 2) + c] = val;
+                }
             }
         }
         float4* o = reinterpret_cast<float4*>(Vp + i * PS);
@@ -54,10 +65,13 @@ __global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restr
     }
 }
 
+// Adjoint of the slice packing for the gradient: node j of component c gets
+// scale * sum_m w_j(m) G_m[node], w_j(m) = 1 - th[m] if j = j[m], th[m] if j = j[m] + 1.
 template <int D>
-__global__ void unpack_velocity_kernel(const float* __restrict__ Gp, float* __restrict__ out, DevGrid g, int K,
-                                       float scale) {
+__global__ void distribute_gradient_kernel(const float* __restrict__ Gp, float* __restrict__ out, DevGrid g, int K,
+                                           SliceTable tab, float scale) {
     const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t nodes = padded_size(g);
     const size_t total = Mv * K;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t s = i % Mv;
@@ -66,17 +80,23 @@ __global__ void unpack_velocity_kernel(const float* __restrict__ Gp, float* __re
         const int y = (int)((s / g.m[0]) % g.m[1]);
         const int z = (int)(s / ((size_t)g.m[0] * g.m[1]));
         const size_t node = ((size_t)(z + (D == 3 ? LGNK_PAD : 0)) * g.mp[1] + (y + LGNK_PAD)) * g.mp[0] + (x + LGNK_PAD);
-        const size_t e = node * K + j;
-        float val[4];
-        if (D == 3) {
-            const float4 a = reinterpret_cast<const float4*>(Gp)[e];
-            val[0] = a.x; val[1] = a.y; val[2] = a.z;
-        } else {
-            const float2 a = reinterpret_cast<const float2*>(Gp)[e];
-            val[0] = a.x; val[1] = a.y;
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int m = 0; m < tab.n; ++m) {
+            float w = 0.0f;
+            if (tab.j[m] == j) w = 1.0f - tab.th[m];
+            else if (tab.j[m] + 1 == j) w = tab.th[m];
+            if (w == 0.0f) continue;
+            const size_t e = (size_t)m * nodes + node;
+            if (D == 3) {
+                const float4 a = reinterpret_cast<const float4*>(Gp)[e];
+                acc[0] = fmaf(w, a.x, acc[0]); acc[1] = fmaf(w, a.y, acc[1]); acc[2] = fmaf(w, a.z, acc[2]);
+            } else {
+                const float2 a = reinterpret_cast<const float2*>(Gp)[e];
+                acc[0] = fmaf(w, a.x, acc[0]); acc[1] = fmaf(w, a.y, acc[1]);
+            }
         }
 #pragma unroll
-        for (int c = 0; c < D; ++c) out[((size_t)j * D + c) * Mv + s] = scale * val[c];
+        for (int c = 0; c < D; ++c) out[((size_t)j * D + c) * Mv + s] = scale * acc[c];
     }
 }
 
@@ -316,19 +336,40 @@ inline int grid_for(size_t count) {
 
 }  // namespace
 
-cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, cudaStream_t s) {
-    const size_t total = (size_t)g.mp[0] * g.mp[1] * g.mp[2] * K;
-    if (d == 3) pack_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, K);
-    else pack_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, K);
+cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, const SliceTable& t,
+                                 cudaStream_t s) {
+    (void)K;
+    const size_t total = (size_t)g.mp[0] * g.mp[1] * g.mp[2] * t.n;
+    if (d == 3) pack_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, t);
+    else pack_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, t);
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_velocity(int d, const void* Gp, float* out, const DevGrid& g, int K, float scale,
-                                   cudaStream_t s) {
+cudaError_t launch_distribute_gradient(int d, const void* Gp, float* out, const DevGrid& g, int K,
+                                       const SliceTable& t, float scale, cudaStream_t s) {
     const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * K;
-    if (d == 3) unpack_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>((const float*)Gp, out, g, K, scale);
-    else unpack_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>((const float*)Gp, out, g, K, scale);
+    if (d == 3) distribute_gradient_kernel<3><<<grid_for(total), kBlock, 0, s>>>((const float*)Gp, out, g, K, t, scale);
+    else distribute_gradient_kernel<2><<<grid_for(total), kBlock, 0, s>>>((const float*)Gp, out, g, K, t, scale);
     return cudaGetLastError();
+}
+
+void make_slice_table(int K, int N, double t0, double dt, SliceTable* t) {
+    if (K <= 1) {
+        t->n = 1;
+        t->j[0] = 0;
+        t->th[0] = 0.0f;
+        return;
+    }
+    t->n = 2 * N + 1;
+    for (int m = 0; m < t->n; ++m) {
+        double tm = t0 + m * 0.5 * dt;
+        tm = tm < 0.0 ? 0.0 : (tm > 1.0 ? 1.0 : tm);
+        const double sv = tm * (K - 1);
+        int j = (int)std::floor(sv);
+        if (j > K - 2) j = K - 2;
+        t->j[m] = j;
+        t->th[m] = (float)(sv - j);
+    }
 }
 
 cudaError_t launch_pack_image(const float* T, float* Tp, const DevGrid& g, int d, float scale, cudaStream_t s) {

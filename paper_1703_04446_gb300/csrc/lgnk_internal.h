@@ -14,6 +14,7 @@
 // (the adjoint of zero extension: splatted mass that leaves the grid is lost).
 #define LGNK_PAD 2
 #define LGNK_MAX_STEPS 64
+#define LGNK_MAX_SLICES (2 * LGNK_MAX_STEPS + 1)
 #define LGNK_BLOCK 256
 
 struct DevGrid {
@@ -32,6 +33,15 @@ inline void trace_tile_shape(int d, int* t) {
     else { t[0] = 16; t[1] = 16; t[2] = 1; }
 }
 
+// Time slices of a velocity: slice m is the field at stage time t0 + m dt / 2,
+// (1 - th[m]) v_j[m] + th[m] v_{j[m]+1} (linear in time between the K nodes);
+// a stationary field (K = 1) has the single slice j = 0, th = 0.
+struct SliceTable {
+    int n;
+    int j[LGNK_MAX_SLICES];
+    float th[LGNK_MAX_SLICES];
+};
+
 // Arguments of one launch of the characteristic-tracing kernel family.
 struct TraceArgs {
     DevGrid ig, vg;
@@ -43,8 +53,9 @@ struct TraceArgs {
     // vxi_a[a] + (i + 1/2) * vxi_b[a]  (exact in FP64: (x_c - lo_v) / h_v - 1/2)
     double vxi_a[3], vxi_b[3];
     float vxi_af[3], vxi_bf[3];  // the same in FP32 (per-stage recomputation)
-    const void* V;            // pair-packed velocity [zp][yp][xp][K] x [v(node) | v(node+1)]
-    const void* dV;           // pair-packed direction (JVP, HESS)
+    long long slice_nodes;    // padded velocity nodes per time slice
+    const void* V;            // pair-packed velocity slices [m][zp][yp][xp] x [v(node) | v(node+1)]
+    const void* dV;           // pair-packed direction slices (JVP, HESS)
     const float* Tp;          // padded template (gathers)
     const float* T;           // template, ABI layout (continuity particle masses)
     const float* R;           // reference, ABI layout (OBJGRAD, FWD with residual)
@@ -52,7 +63,7 @@ struct TraceArgs {
     float* u1;                // transport FWD output (ABI layout)
     float* yout;              // optional end points [d][M]
     float* acc;               // continuity splat accumulator (padded image)
-    void* G;                  // gradient accumulator [zp][yp][xp][K] of float4 (3D) / float2 (2D)
+    void* G;                  // gradient accumulator slices [m][zp][yp][xp] of float4 (3D) / float2 (2D)
     double* partial;          // per-block FP64 partial sums of res^2
 };
 
@@ -61,11 +72,16 @@ cudaError_t launch_trace(int d, bool nonstat, int model, int mode, const TraceAr
                          cudaStream_t s);
 
 // grid utilities (grid_ops.cu)
-// ABI velocity -> pair-packed padded layout (pair_bytes(d) bytes per node and time node)
-cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, cudaStream_t s);
+// ABI velocity [K][d][z][y][x] -> pair-packed padded time slices
+// (velocity_pair_bytes(d) bytes per node and slice)
+cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, const SliceTable& t,
+                                 cudaStream_t s);
 inline size_t velocity_pair_bytes(int d) { return d == 3 ? 32 : 16; }
-cudaError_t launch_unpack_velocity(int d, const void* Gp, float* out, const DevGrid& g, int K,
-                                   float scale, cudaStream_t s);
+// slice gradients [m][padded nodes] -> ABI [K][d][z][y][x], out = scale * sum_m w_j(m) G_m
+cudaError_t launch_distribute_gradient(int d, const void* Gp, float* out, const DevGrid& g, int K,
+                                       const SliceTable& t, float scale, cudaStream_t s);
+// stage-time slices of a trace with N steps from t0 in steps dt, over K time nodes
+void make_slice_table(int K, int N, double t0, double dt, SliceTable* t);
 cudaError_t launch_pack_image(const float* T, float* Tp, const DevGrid& g, int d, float scale, cudaStream_t s);
 cudaError_t launch_unpack_image(const float* acc, float* out, const DevGrid& g, int d, cudaStream_t s);
 cudaError_t launch_repad_image(float* acc, const DevGrid& g, int d, float scale, cudaStream_t s);

@@ -85,7 +85,9 @@ extern "C" lgnk_status lgnk_forward_transport_static(const lgnk_problem* prob, c
         tiles[i] = (ig.m[i] + ts[i] - 1) / ts[i];
         nblocks *= tiles[i];
     }
-    const size_t vbytes = align256((size_t)vg.mp[0] * vg.mp[1] * vg.mp[2] * K * velocity_pair_bytes(d));
+    SliceTable slices;
+    make_slice_table(K, prob->rk4_steps, 1.0, -1.0 / prob->rk4_steps, &slices);
+    const size_t vbytes = align256((size_t)vg.mp[0] * vg.mp[1] * vg.mp[2] * slices.n * velocity_pair_bytes(d));
     const size_t tbytes = align256((size_t)ig.mp[0] * ig.mp[1] * ig.mp[2] * sizeof(float));
     const size_t pbytes = align256((size_t)nblocks * sizeof(double));
     const size_t need = vbytes + tbytes + pbytes + 256;
@@ -108,7 +110,7 @@ extern "C" lgnk_status lgnk_forward_transport_static(const lgnk_problem* prob, c
     // Every scratch byte a launch reads is written earlier in the same call
     // (packing writes pads and interiors, each block writes its partial), so
     // nothing left by a previous call needs clearing.
-    cudaError_t e = launch_pack_velocity(d, v, Vp, vg, K, s);
+    cudaError_t e = launch_pack_velocity(d, v, Vp, vg, K, slices, s);
     if (e == cudaSuccess) e = launch_pack_image(T, Tp, ig, d, 1.0f, s);
     TraceArgs a{};
     a.ig = ig;
@@ -131,6 +133,7 @@ extern "C" lgnk_status lgnk_forward_transport_static(const lgnk_problem* prob, c
         }
     }
     a.cellvol = (float)cellvol;
+    a.slice_nodes = (long long)vg.mp[0] * vg.mp[1] * vg.mp[2];
     a.V = Vp;
     a.Tp = Tp;
     a.R = R;

@@ -31,9 +31,18 @@
 // is the gradient of the scalar interpolant of v . mu (corners contracted with
 // mu first).  No d x d matrix lives in registers.
 //
-// Gradient scatter.  (d_v I)^T mu goes to the padded gradient accumulator with
-// one vector reduction (red.global.add.v4.f32 / .v2) per corner, executed by
-// the L2 atomic units; consecutive stages in the same cell are combined first.  A shared-memory tile of the velocity grid was measured
+// Time slices.  Every RK4 stage time is t0 + m dt/2 (m = 0..2N), so the host
+// packs the velocity (and the direction) at those 2N + 1 times, linearly
+// interpolated between its K time nodes, as slices [m][node].  A stage reads
+// the one slice of its time: a non-stationary field costs the same gathers as
+// a stationary one (K = 1: a single slice), and no time interpolation happens
+// in the kernels.
+//
+// Gradient scatter.  (d_v I)^T mu goes to the padded gradient accumulator of
+// the stage's slice with one vector reduction (red.global.add.v4.f32 / .v2)
+// per corner, executed by the L2 atomic units; consecutive stages in the same
+// cell and slice are combined first.  The host then distributes the slices
+// onto the K time nodes with the transposed time weights.  A shared-memory tile of the velocity grid was measured
 // slower: float atomics on shared memory retry under the heavy same-address
 // contention of neighbouring characteristics.
 #pragma once
@@ -46,37 +55,11 @@ template <int D> struct VecT;
 template <> struct VecT<2> { using type = float2; };
 template <> struct VecT<3> { using type = float4; };
 
-__device__ __forceinline__ void load_vec(const float2* p, float* o) {
-    const float2 a = __ldg(p);
-    o[0] = a.x; o[1] = a.y;
-}
-__device__ __forceinline__ void load_vec(const float4* p, float* o) {
-    const float4 a = __ldg(p);
-    o[0] = a.x; o[1] = a.y; o[2] = a.z;
-}
 __device__ __forceinline__ void red_vec(float2* p, const float* x, float w) {
     atomicAdd(p, make_float2(w * x[0], w * x[1]));
 }
 __device__ __forceinline__ void red_vec(float4* p, const float* x, float w) {
     atomicAdd(p, make_float4(w * x[0], w * x[1], w * x[2], 0.0f));
-}
-
-// Start of one characteristic on one grid: its continuous grid index I0 + F0.
-// Offsets t = F0 + u / h are clamped to [-2 - I0, m - I0 + 1/2], which keeps
-// the lower corner I0 + floor(t) in [-2, m].
-template <int D>
-struct Start {
-    int I0[D];
-    float F0[D];
-};
-
-template <int D>
-__device__ __forceinline__ void start_on_image(const int* idx, Start<D>& s) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        s.I0[a] = idx[a];
-        s.F0[a] = 0.0f;
-    }
 }
 
 template <int D> struct TileShape;
@@ -97,6 +80,24 @@ __device__ __forceinline__ void voxel_index(const TraceArgs& A, int* idx) {
     idx[0] = bx * TS::X + t % TS::X;
     idx[1] = by * TS::Y + (t / TS::X) % TS::Y;
     idx[2] = bz * TS::Z + t / (TS::X * TS::Y);
+}
+
+// Start of one characteristic on one grid: its continuous grid index I0 + F0.
+// Offsets t = F0 + u / h are clamped to [-2 - I0, m - I0 + 1/2], which keeps
+// the lower corner I0 + floor(t) in [-2, m].
+template <int D>
+struct Start {
+    int I0[D];
+    float F0[D];
+};
+
+template <int D>
+__device__ __forceinline__ void start_on_image(const int* idx, Start<D>& s) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        s.I0[a] = idx[a];
+        s.F0[a] = 0.0f;
+    }
 }
 
 // Start of this thread's characteristic on the velocity grid:
@@ -165,15 +166,6 @@ __device__ __forceinline__ float corner_weight(int c, const float* f, const DevG
     return w;
 }
 
-// Time slot of stage time t: nodes t_j = j/(K-1), weight th on node j+1.
-__device__ __forceinline__ void time_slot(int K, float t, int& j, float& th) {
-    if (K == 1) { j = 0; th = 0.0f; return; }
-    const float s = fminf(fmaxf(t, 0.0f), 1.0f) * (float)(K - 1);
-    const int jj = min((int)floorf(s), K - 2);
-    j = jj;
-    th = s - (float)jj;
-}
-
 // Both x-corners of a cell row from the pair-packed velocity: element e holds
 // [v(node) | v(node + 1)] (3D: 32 bytes, one 256-bit load; 2D: 16 bytes).
 __device__ __forceinline__ void load_pair3(const float* p, float* a, float* b) {
@@ -182,8 +174,8 @@ __device__ __forceinline__ void load_pair3(const float* p, float* a, float* b) {
         : "l"(p));
 }
 
-template <int D, bool NS>
-__device__ __forceinline__ void pair_value(const float* __restrict__ V, size_t e, float th, float* a, float* b) {
+template <int D>
+__device__ __forceinline__ void pair_value(const float* __restrict__ V, size_t e, float* a, float* b) {
     constexpr int PS = (D == 3) ? 8 : 4;
     if (D == 3) {
         load_pair3(V + e * PS, a, b);
@@ -191,40 +183,27 @@ __device__ __forceinline__ void pair_value(const float* __restrict__ V, size_t e
         const float4 t = __ldg(reinterpret_cast<const float4*>(V + e * PS));
         a[0] = t.x; a[1] = t.y; b[0] = t.z; b[1] = t.w;
     }
-    if (NS) {
-        float a1[3], b1[3];
-        if (D == 3) {
-            load_pair3(V + (e + 1) * PS, a1, b1);
-        } else {
-            const float4 t = __ldg(reinterpret_cast<const float4*>(V + (e + 1) * PS));
-            a1[0] = t.x; a1[1] = t.y; b1[0] = t.z; b1[1] = t.w;
-        }
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-            a[q] = fmaf(th, a1[q] - a[q], a[q]);
-            b[q] = fmaf(th, b1[q] - b[q], b[q]);
-        }
-    }
 }
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
 
-// Element index of corner (cx, cy, cz) of the cell with lower corner `base`.
-template <int D, bool NS>
-__device__ __forceinline__ size_t corner_elem(const DevGrid& g, int base, int cx, int cy, int cz, int K, int jt) {
+// Element of corner (0, cy, cz) of the cell with lower corner `base` in the
+// slice starting at element `s0`.
+template <int D>
+__device__ __forceinline__ size_t corner_elem(const DevGrid& g, size_t s0, int base, int cx, int cy, int cz) {
     int o = base + cx + cy * g.mp[0];
     if (D == 3) o += cz * g.mp[0] * g.mp[1];
-    return NS ? (size_t)o * K + jt : (size_t)o;   // stationary: K = 1
+    return s0 + (size_t)o;
 }
 
 // One plane (fixed z corner) of the cell: bilinear value and the unscaled
 // derivatives along the fractional x and y offsets, per component.
-template <int D, bool NS, bool GRAD>
-__device__ __forceinline__ void plane(const DevGrid& g, int K, const float* __restrict__ V, int base, int cz, int jt,
-                                      float th, const float* f, float* val, float* dx, float* dy) {
+template <int D, bool GRAD>
+__device__ __forceinline__ void plane(const DevGrid& g, const float* __restrict__ V, size_t s0, int base, int cz,
+                                      const float* f, float* val, float* dx, float* dy) {
     float c00[3], c10[3], c01[3], c11[3];
-    pair_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 0, cz, K, jt), th, c00, c10);
-    pair_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, 1, cz, K, jt), th, c01, c11);
+    pair_value<D>(V, corner_elem<D>(g, s0, base, 0, 0, cz), c00, c10);
+    pair_value<D>(V, corner_elem<D>(g, s0, base, 0, 1, cz), c01, c11);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
         const float a0 = lerp(c00[q], c10[q], f[0]);
@@ -238,15 +217,14 @@ __device__ __forceinline__ void plane(const DevGrid& g, int K, const float* __re
 }
 
 // Scalar version: corner values contracted with mu first (s_c = v_c . mu).
-template <int D, bool NS>
-__device__ __forceinline__ void plane_dot(const DevGrid& g, int K, const float* __restrict__ V, int base, int cz,
-                                          int jt, float th, const float* f, const float* mu, float& val, float& dx,
-                                          float& dy) {
+template <int D>
+__device__ __forceinline__ void plane_dot(const DevGrid& g, const float* __restrict__ V, size_t s0, int base, int cz,
+                                          const float* f, const float* mu, float& val, float& dx, float& dy) {
     float c[4];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         float a[3], b[3];
-        pair_value<D, NS>(V, corner_elem<D, NS>(g, base, 0, r, cz, K, jt), th, a, b);
+        pair_value<D>(V, corner_elem<D>(g, s0, base, 0, r, cz), a, b);
         float sa = 0.0f, sb = 0.0f;
 #pragma unroll
         for (int q = 0; q < D; ++q) {
@@ -263,35 +241,35 @@ __device__ __forceinline__ void plane_dot(const DevGrid& g, int K, const float* 
     dy = a1 - a0;
 }
 
-// val = I(v, y, t) (Sec. 3.1, Step 1: multilinear in space, linear in time).
-template <int D, bool NS>
-__device__ __forceinline__ void stage_value(const DevGrid& g, int K, const float* __restrict__ V, const int* p, const float* f,
-                                            int jt, float th, float* val) {
+// val = I(v, y, t) at the slice of t (Sec. 3.1, Step 1: multilinear in space,
+// linear in time through the slice).
+template <int D>
+__device__ __forceinline__ void stage_value(const DevGrid& g, const float* __restrict__ V, size_t s0, const int* p,
+                                            const float* f, float* val) {
     const int base = linear<D>(g, p);
-    plane<D, NS, false>(g, K, V, base, 0, jt, th, f, val, nullptr, nullptr);
+    plane<D, false>(g, V, s0, base, 0, f, val, nullptr, nullptr);
     if (D == 3) {
         float v1[D];
-        plane<D, NS, false>(g, K, V, base, 1, jt, th, f, v1, nullptr, nullptr);
+        plane<D, false>(g, V, s0, base, 1, f, v1, nullptr, nullptr);
 #pragma unroll
         for (int q = 0; q < D; ++q) val[q] = lerp(val[q], v1[q], f[D - 1]);
     }
 }
 
 // Tangent stage: val = I(v, y, t), Jq = d_y I(v, y, t) q, dval = I(dv, y, t).
-template <int D, bool NS>
-__device__ __forceinline__ void stage_tangent(const DevGrid& g, int K, const float* __restrict__ V,
-                                              const float* __restrict__ dV, const int* p,
-                                              const float* f, int jt, float th, const float* qv, float* val,
-                                              float* Jq, float* dval) {
+template <int D>
+__device__ __forceinline__ void stage_tangent(const DevGrid& g, const float* __restrict__ V,
+                                              const float* __restrict__ dV, size_t s0, const int* p, const float* f,
+                                              const float* qv, float* val, float* Jq, float* dval) {
     const int base = linear<D>(g, p);
     float qs[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) qs[a] = qv[a] * g.inv_h[a];
     float dx[D], dy[D];
-    plane<D, NS, true>(g, K, V, base, 0, jt, th, f, val, dx, dy);
+    plane<D, true>(g, V, s0, base, 0, f, val, dx, dy);
     if (D == 3) {
         float v1[D], dx1[D], dy1[D];
-        plane<D, NS, true>(g, K, V, base, 1, jt, th, f, v1, dx1, dy1);
+        plane<D, true>(g, V, s0, base, 1, f, v1, dx1, dy1);
 #pragma unroll
         for (int q = 0; q < D; ++q) {
             const float dz = v1[q] - val[q];
@@ -306,27 +284,26 @@ __device__ __forceinline__ void stage_tangent(const DevGrid& g, int K, const flo
     }
 #pragma unroll
     for (int q = 0; q < D; ++q) Jq[q] = fmaf(dx[q], qs[0], fmaf(dy[q], qs[1], Jq[q]));
-    stage_value<D, NS>(g, K, dV, p, f, jt, th, dval);
+    stage_value<D>(g, dV, s0, p, f, dval);
 }
 
 // Destination of the adjoint scatter (d_v I)^T mu: the padded gradient
-// accumulator, with a one-entry write-combining slot.  Consecutive adjoint
-// stages of a characteristic usually fall in the same velocity cell (and time
-// slot); their contributions w_c(f) mu are then summed per corner and sent as
-// one vector reduction instead of two.
+// accumulator of each slice, with a one-entry write-combining slot.
+// Consecutive adjoint stages of a characteristic usually fall in the same
+// velocity cell and slice; their contributions w_c(f) mu are then summed per
+// corner and sent as one vector reduction instead of two.
 template <int D>
 struct Scatter {
     typename VecT<D>::type* G;
-    int base;       // cell of the pending contribution, -1 if none
-    int jt;
-    float th;
+    size_t s0;      // slice of the pending contribution
+    int base;       // its cell, -1 if none
     float f[D];
     float mu[D];
 };
 
-template <int D, bool NS>
-__device__ __forceinline__ void scatter_flush(const DevGrid& g, int K, Scatter<D>& S, bool two, const float* f2,
-                                              const float* mu2, float th2) {
+template <int D>
+__device__ __forceinline__ void scatter_flush(const DevGrid& g, Scatter<D>& S, bool two, const float* f2,
+                                              const float* mu2) {
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
         float w = (c & 1 ? S.f[0] : 1.0f - S.f[0]) * ((c >> 1) & 1 ? S.f[1] : 1.0f - S.f[1]);
@@ -336,36 +313,26 @@ __device__ __forceinline__ void scatter_flush(const DevGrid& g, int K, Scatter<D
             w2 = (c & 1 ? f2[0] : 1.0f - f2[0]) * ((c >> 1) & 1 ? f2[1] : 1.0f - f2[1]);
             if (D == 3) w2 *= ((c >> 2) & 1) ? f2[D - 1] : 1.0f - f2[D - 1];
         }
-        const size_t e = corner_elem<D, NS>(g, S.base, c & 1, (c >> 1) & 1, (c >> 2) & 1, K, S.jt);
+        const size_t e = corner_elem<D>(g, S.s0, S.base, c & 1, (c >> 1) & 1, (c >> 2) & 1);
         float x[D];
-        if (NS) {
 #pragma unroll
-            for (int q = 0; q < D; ++q) x[q] = w * (1.0f - S.th) * S.mu[q] + w2 * (1.0f - th2) * mu2[q];
-            red_vec(S.G + e, x, 1.0f);
-#pragma unroll
-            for (int q = 0; q < D; ++q) x[q] = w * S.th * S.mu[q] + w2 * th2 * mu2[q];
-            red_vec(S.G + e + 1, x, 1.0f);
-        } else {
-#pragma unroll
-            for (int q = 0; q < D; ++q) x[q] = fmaf(w2, mu2[q], w * S.mu[q]);
-            red_vec(S.G + e, x, 1.0f);
-        }
+        for (int q = 0; q < D; ++q) x[q] = fmaf(w2, two ? mu2[q] : 0.0f, w * S.mu[q]);
+        red_vec(S.G + e, x, 1.0f);
     }
     S.base = -1;
 }
 
-// Add the contribution w_c(f) mu at cell `base`, time slot (jt, th).
-template <int D, bool NS>
-__device__ __forceinline__ void scatter_add(const DevGrid& g, int K, Scatter<D>& S, int base, const float* f,
-                                            int jt, float th, const float* mu) {
-    if (S.base == base && S.jt == jt) {
-        scatter_flush<D, NS>(g, K, S, true, f, mu, th);
+// Add the contribution w_c(f) mu at cell `base` of slice `s0`.
+template <int D>
+__device__ __forceinline__ void scatter_add(const DevGrid& g, Scatter<D>& S, size_t s0, int base, const float* f,
+                                            const float* mu) {
+    if (S.base == base && S.s0 == s0) {
+        scatter_flush<D>(g, S, true, f, mu);
         return;
     }
-    if (S.base >= 0) scatter_flush<D, NS>(g, K, S, false, f, mu, th);
+    if (S.base >= 0) scatter_flush<D>(g, S, false, f, mu);
     S.base = base;
-    S.jt = jt;
-    S.th = th;
+    S.s0 = s0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         S.f[a] = f[a];
@@ -373,25 +340,24 @@ __device__ __forceinline__ void scatter_add(const DevGrid& g, int K, Scatter<D>&
     }
 }
 
-// Adjoint stage: scatter w_c * (time weight) * mu into the gradient and return
+// Adjoint stage: scatter w_c mu into the slice's gradient and return
 // nu = d_y I(v, y, t)^T mu = grad_y (v . mu) of the interpolant.
-template <int D, bool NS>
-__device__ __forceinline__ void stage_adjoint(const DevGrid& g, int K, const float* __restrict__ V,
-                                              Scatter<D>& S, const int* p, const float* f, int jt, float th,
-                                              const float* mu, float* nu) {
+template <int D>
+__device__ __forceinline__ void stage_adjoint(const DevGrid& g, const float* __restrict__ V, Scatter<D>& S,
+                                              size_t s0, const int* p, const float* f, const float* mu, float* nu) {
     const int base = linear<D>(g, p);
-    float s0, dx, dy;
-    plane_dot<D, NS>(g, K, V, base, 0, jt, th, f, mu, s0, dx, dy);
+    float s_0, dx, dy;
+    plane_dot<D>(g, V, s0, base, 0, f, mu, s_0, dx, dy);
     if (D == 3) {
-        float s1, dx1, dy1;
-        plane_dot<D, NS>(g, K, V, base, 1, jt, th, f, mu, s1, dx1, dy1);
-        nu[D - 1] = (s1 - s0) * g.inv_h[D - 1];
+        float s_1, dx1, dy1;
+        plane_dot<D>(g, V, s0, base, 1, f, mu, s_1, dx1, dy1);
+        nu[D - 1] = (s_1 - s_0) * g.inv_h[D - 1];
         dx = lerp(dx, dx1, f[D - 1]);
         dy = lerp(dy, dy1, f[D - 1]);
     }
     nu[0] = dx * g.inv_h[0];
     nu[1] = dy * g.inv_h[1];
-    scatter_add<D, NS>(g, K, S, base, f, jt, th, mu);
+    scatter_add<D>(g, S, s0, base, f, mu);
 }
 
 // T(y) and optionally grad T(y) from the padded image, y at displacement u.
@@ -446,50 +412,44 @@ __device__ __forceinline__ void splat_image(const DevGrid& g, const Start<D>& s,
     }
 }
 
-struct Slots {
-    int j1, j2, j4;
-    float th1, th2, th4;
-};
-
+// Slices of the stages of step k: t_k (2k), t_k + dt/2 (2k + 1, stages 2 and
+// 3), t_k + dt (2k + 2); a stationary field has the single slice 0.
 template <bool NS>
-__device__ __forceinline__ Slots step_slots(const TraceArgs& A, float tk) {
-    Slots s;
-    if (!NS) {
-        s.j1 = s.j2 = s.j4 = 0;
-        s.th1 = s.th2 = s.th4 = 0.0f;
-        return s;
+__device__ __forceinline__ void step_slices(const TraceArgs& A, int k, size_t& s1, size_t& s2, size_t& s4) {
+    if (NS) {
+        s1 = (size_t)(2 * k) * A.slice_nodes;
+        s2 = s1 + A.slice_nodes;
+        s4 = s2 + A.slice_nodes;
+    } else {
+        s1 = s2 = s4 = 0;
     }
-    time_slot(A.K, tk, s.j1, s.th1);
-    time_slot(A.K, tk + 0.5f * A.dt, s.j2, s.th2);
-    time_slot(A.K, tk + A.dt, s.j4, s.th4);
-    return s;
 }
 
 // One RK4 step of the characteristic (Alg. 1 without the derivative), on the
 // displacement u.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u,
-                                         float tk) {
-    const Slots sl = step_slots<NS>(A, tk);
+__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u, int k) {
+    size_t s1, s2, s4;
+    step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
     start_on_velocity<D>(A, sv);
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
     float f[D], vs[D], us[D], acc[D];
     locate<D>(A.vg, sv, u, p, f);
-    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j1, sl.th1, vs);
+    stage_value<D>(A.vg, V, s1, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = vs[a]; us[a] = fmaf(hdt, vs[a], u[a]); }
     locate<D>(A.vg, sv, us, p, f);
-    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
+    stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(hdt, vs[a], u[a]); }
     locate<D>(A.vg, sv, us, p, f);
-    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
+    stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(dt, vs[a], u[a]); }
     locate<D>(A.vg, sv, us, p, f);
-    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j4, sl.th4, vs);
+    stage_value<D>(A.vg, V, s4, p, f, vs);
     const float s6 = dt / 6.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) u[a] = fmaf(s6, acc[a] + vs[a], u[a]);
@@ -499,9 +459,9 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
 template <int D, bool NS>
 __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float* V, const float* dV, float* u,
-                                                 float* dy,
-                                                 float tk) {
-    const Slots sl = step_slots<NS>(A, tk);
+                                                 float* dy, int k) {
+    size_t s1, s2, s4;
+    step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
     start_on_velocity<D>(A, sv);
     const float dt = A.dt, hdt = 0.5f * A.dt;
@@ -509,7 +469,7 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
     float f[D], us[D], q[D], vs[D], Jq[D], dvs[D], sv_acc[D], sd_acc[D], Ds;
     // stage 1 at y, offset dy
     locate<D>(A.vg, sv, u, p, f);
-    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j1, sl.th1, dy, vs, Jq, dvs);
+    stage_tangent<D>(A.vg, V, dV, s1, p, f, dy, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Ds = dvs[a] + Jq[a];
@@ -520,7 +480,7 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
     }
     // stage 2
     locate<D>(A.vg, sv, us, p, f);
-    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j2, sl.th2, q, vs, Jq, dvs);
+    stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Ds = dvs[a] + Jq[a];
@@ -531,7 +491,7 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
     }
     // stage 3
     locate<D>(A.vg, sv, us, p, f);
-    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j2, sl.th2, q, vs, Jq, dvs);
+    stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Ds = dvs[a] + Jq[a];
@@ -542,7 +502,7 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
     }
     // stage 4
     locate<D>(A.vg, sv, us, p, f);
-    stage_tangent<D, NS>(A.vg, A.K, V, dV, p, f, sl.j4, sl.th4, q, vs, Jq, dvs);
+    stage_tangent<D>(A.vg, V, dV, s4, p, f, q, vs, Jq, dvs);
     const float s6 = dt / 6.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -556,24 +516,25 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
 // its start.  Stage positions are recomputed from the step start u; each
 // stage's J^T mu and scatter share one pass over its corners.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V,
-                                                 Scatter<D>& S, const float* u, float* lam, float tk) {
-    const Slots sl = step_slots<NS>(A, tk);
+__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, Scatter<D>& S, const float* u,
+                                                 float* lam, int k) {
+    size_t s1, s2, s4;
+    step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
     start_on_velocity<D>(A, sv);
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
     float f[D], vs[D], u2[D], u3[D], u4[D];
     locate<D>(A.vg, sv, u, p, f);
-    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j1, sl.th1, vs);
+    stage_value<D>(A.vg, V, s1, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) u2[a] = fmaf(hdt, vs[a], u[a]);
     locate<D>(A.vg, sv, u2, p, f);
-    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
+    stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) u3[a] = fmaf(hdt, vs[a], u[a]);
     locate<D>(A.vg, sv, u3, p, f);
-    stage_value<D, NS>(A.vg, A.K, V, p, f, sl.j2, sl.th2, vs);
+    stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) u4[a] = fmaf(dt, vs[a], u[a]);
 
@@ -583,22 +544,22 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float
 #pragma unroll
     for (int a = 0; a < D; ++a) mu[a] = c16 * lam[a];
     locate<D>(A.vg, sv, u4, p, f);
-    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j4, sl.th4, mu, nu);
+    stage_adjoint<D>(A.vg, V, S, s4, p, f, mu, nu);
     // stage 3: D3 = I(dv, y3) + J3 (dy + dt/2 D2)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); }
     locate<D>(A.vg, sv, u3, p, f);
-    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j2, sl.th2, mu, nu);
+    stage_adjoint<D>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 2: D2 = I(dv, y2) + J2 (dy + dt/2 D1)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); }
     locate<D>(A.vg, sv, u2, p, f);
-    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j2, sl.th2, mu, nu);
+    stage_adjoint<D>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 1: D1 = I(dv, y) + J1 dy
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); }
     locate<D>(A.vg, sv, u, p, f);
-    stage_adjoint<D, NS>(A.vg, A.K, V, S, p, f, sl.j1, sl.th1, mu, nu);
+    stage_adjoint<D>(A.vg, V, S, s1, p, f, mu, nu);
 #pragma unroll
     for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
 }
@@ -620,12 +581,11 @@ __device__ __forceinline__ double block_sum(double x) {
     return s;
 }
 
-template <int D, bool NS, int MODEL, int MODE>
 // 256 threads; FWD at 64 registers (4 CTAs per SM), the derivative modes at 80
 // (3 CTAs): measured fastest among 64/80/128-register and 256/512-thread
 // configurations on the 128^3 matvec.
-__global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
-    trace_kernel(const TraceArgs A) {
+template <int D, bool NS, int MODEL, int MODE>
+__global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_kernel(const TraceArgs A) {
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
     constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD);
@@ -640,6 +600,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
     Scatter<D> S;
     S.G = static_cast<VT*>(A.G);
     S.base = -1;
+    S.s0 = 0;
 
     if (active) {
         const int vox = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
@@ -653,13 +614,12 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
 
 #pragma unroll 1
         for (int k = 0; k < A.N; ++k) {
-            const float tk = A.t0 + (float)k * A.dt;
             if (ADJOINT) {
 #pragma unroll
                 for (int a = 0; a < D; ++a) hist[ADJOINT ? k : 0][a] = u[a];
             }
-            if (TANGENT) rk4_tangent_step<D, NS>(A, V, dV, u, dy, tk);
-            else rk4_step<D, NS>(A, V, u, tk);
+            if (TANGENT) rk4_tangent_step<D, NS>(A, V, dV, u, dy, k);
+            else rk4_step<D, NS>(A, V, u, k);
         }
         if (A.yout != nullptr) {
             const int M = A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
@@ -726,11 +686,8 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3)
 
         if (ADJOINT) {
 #pragma unroll 1
-            for (int k = A.N - 1; k >= 0; --k) {
-                const float tk = A.t0 + (float)k * A.dt;
-                rk4_adjoint_step<D, NS>(A, V, S, hist[ADJOINT ? k : 0], lam, tk);
-            }
-            if (S.base >= 0) scatter_flush<D, NS>(A.vg, A.K, S, false, S.f, S.mu, S.th);
+            for (int k = A.N - 1; k >= 0; --k) rk4_adjoint_step<D, NS>(A, V, S, hist[ADJOINT ? k : 0], lam, k);
+            if (S.base >= 0) scatter_flush<D>(A.vg, S, false, S.f, S.mu);
         }
     }
 
