@@ -427,8 +427,8 @@ __device__ __forceinline__ void step_slices(const TraceArgs& A, int k, size_t& s
 
 // One RK4 step of the characteristic (Alg. 1 without the derivative), on the
 // displacement u.
-template <int D, bool NS>
-__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u, int k) {
+template <int D, bool NS, bool REC>
+__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u, int k, float* rec) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -436,18 +436,34 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
     float f[D], vs[D], us[D], acc[D];
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[a] = u[a];
+    }
     locate<D>(A.vg, sv, u, p, f);
     stage_value<D>(A.vg, V, s1, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = vs[a]; us[a] = fmaf(hdt, vs[a], u[a]); }
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[D + a] = us[a];
+    }
     locate<D>(A.vg, sv, us, p, f);
     stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(hdt, vs[a], u[a]); }
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[2 * D + a] = us[a];
+    }
     locate<D>(A.vg, sv, us, p, f);
     stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(dt, vs[a], u[a]); }
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[3 * D + a] = us[a];
+    }
     locate<D>(A.vg, sv, us, p, f);
     stage_value<D>(A.vg, V, s4, p, f, vs);
     const float s6 = dt / 6.0f;
@@ -457,9 +473,9 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
 
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
-template <int D, bool NS>
+template <int D, bool NS, bool REC>
 __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float* V, const float* dV, float* u,
-                                                 float* dy, int k) {
+                                                 float* dy, int k, float* rec) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -468,6 +484,10 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
     int p[D];
     float f[D], us[D], q[D], vs[D], Jq[D], dvs[D], sv_acc[D], sd_acc[D], Ds;
     // stage 1 at y, offset dy
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[a] = u[a];
+    }
     locate<D>(A.vg, sv, u, p, f);
     stage_tangent<D>(A.vg, V, dV, s1, p, f, dy, vs, Jq, dvs);
 #pragma unroll
@@ -479,6 +499,10 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         q[a] = fmaf(hdt, Ds, dy[a]);
     }
     // stage 2
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[D + a] = us[a];
+    }
     locate<D>(A.vg, sv, us, p, f);
     stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
@@ -490,6 +514,10 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         q[a] = fmaf(hdt, Ds, dy[a]);
     }
     // stage 3
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[2 * D + a] = us[a];
+    }
     locate<D>(A.vg, sv, us, p, f);
     stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
@@ -501,6 +529,10 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         q[a] = fmaf(dt, Ds, dy[a]);
     }
     // stage 4
+    if (REC) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[3 * D + a] = us[a];
+    }
     locate<D>(A.vg, sv, us, p, f);
     stage_tangent<D>(A.vg, V, dV, s4, p, f, q, vs, Jq, dvs);
     const float s6 = dt / 6.0f;
@@ -513,10 +545,10 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
 
 // Transpose of one tangent step: given lam (adjoint of the step's end point),
 // scatter the step's contribution into the gradient and return the adjoint of
-// its start.  Stage positions are recomputed from the step start u; each
-// stage's J^T mu and scatter share one pass over its corners.
+// its start.  The stage positions u, u2, u3, u4 were recorded by the forward
+// sweep; each stage's J^T mu and scatter share one pass over its corners.
 template <int D, bool NS>
-__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, Scatter<D>& S, const float* u,
+__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, Scatter<D>& S, const float* rec,
                                                  float* lam, int k) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
@@ -524,41 +556,28 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float
     start_on_velocity<D>(A, sv);
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
-    float f[D], vs[D], u2[D], u3[D], u4[D];
-    locate<D>(A.vg, sv, u, p, f);
-    stage_value<D>(A.vg, V, s1, p, f, vs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) u2[a] = fmaf(hdt, vs[a], u[a]);
-    locate<D>(A.vg, sv, u2, p, f);
-    stage_value<D>(A.vg, V, s2, p, f, vs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) u3[a] = fmaf(hdt, vs[a], u[a]);
-    locate<D>(A.vg, sv, u3, p, f);
-    stage_value<D>(A.vg, V, s2, p, f, vs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) u4[a] = fmaf(dt, vs[a], u[a]);
-
+    float f[D], us[D];
     float mu[D], nu[D], acc[D];
     const float c16 = dt / 6.0f, c13 = dt / 3.0f;
     // stage 4: D4 = I(dv, y4) + J4 (dy + dt D3)
 #pragma unroll
-    for (int a = 0; a < D; ++a) mu[a] = c16 * lam[a];
-    locate<D>(A.vg, sv, u4, p, f);
+    for (int a = 0; a < D; ++a) { mu[a] = c16 * lam[a]; us[a] = rec[3 * D + a]; }
+    locate<D>(A.vg, sv, us, p, f);
     stage_adjoint<D>(A.vg, V, S, s4, p, f, mu, nu);
     // stage 3: D3 = I(dv, y3) + J3 (dy + dt/2 D2)
 #pragma unroll
-    for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); }
-    locate<D>(A.vg, sv, u3, p, f);
+    for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); us[a] = rec[2 * D + a]; }
+    locate<D>(A.vg, sv, us, p, f);
     stage_adjoint<D>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 2: D2 = I(dv, y2) + J2 (dy + dt/2 D1)
 #pragma unroll
-    for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); }
-    locate<D>(A.vg, sv, u2, p, f);
+    for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); us[a] = rec[D + a]; }
+    locate<D>(A.vg, sv, us, p, f);
     stage_adjoint<D>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 1: D1 = I(dv, y) + J1 dy
 #pragma unroll
-    for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); }
-    locate<D>(A.vg, sv, u, p, f);
+    for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); us[a] = rec[a]; }
+    locate<D>(A.vg, sv, us, p, f);
     stage_adjoint<D>(A.vg, V, S, s1, p, f, mu, nu);
 #pragma unroll
     for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
@@ -610,16 +629,14 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_ke
             u[a] = 0.0f;
             dy[a] = 0.0f;
         }
-        float hist[ADJOINT ? LGNK_MAX_STEPS : 1][D];
+        // stage positions of every step (recorded for the adjoint sweep)
+        float hist[ADJOINT ? LGNK_MAX_STEPS : 1][4 * D];
 
 #pragma unroll 1
         for (int k = 0; k < A.N; ++k) {
-            if (ADJOINT) {
-#pragma unroll
-                for (int a = 0; a < D; ++a) hist[ADJOINT ? k : 0][a] = u[a];
-            }
-            if (TANGENT) rk4_tangent_step<D, NS>(A, V, dV, u, dy, k);
-            else rk4_step<D, NS>(A, V, u, k);
+            float* rec = hist[ADJOINT ? k : 0];
+            if (TANGENT) rk4_tangent_step<D, NS, ADJOINT>(A, V, dV, u, dy, k, rec);
+            else rk4_step<D, NS, ADJOINT>(A, V, u, k, rec);
         }
         if (A.yout != nullptr) {
             const int M = A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
