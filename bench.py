@@ -169,9 +169,10 @@ def algorithmic_bytes_hess(wl):
 # FP32 FLOPs (FMA = 2) of one voxel-step of the fused matvec in 3D for a
 # stationary velocity, counted from the separable trilinear evaluation: tangent
 # step 4 x (gradient planes, z-combination, J q, dv value, locate) plus state
-# updates = 849; adjoint step 3 value stages + 4 dot-gradient stages + scatter
-# weights/products + bookkeeping = 832.
-HESS_FLOPS_PER_VOXEL_STEP = 1680
+# updates = 849; adjoint step 4 x (dot-gradient stage, locate, scatter weights
+# and products) plus bookkeeping = 574 (stage positions are recorded by the
+# tangent sweep, not recomputed).
+HESS_FLOPS_PER_VOXEL_STEP = 1423
 
 
 def algorithmic_flops_hess(wl):
@@ -217,6 +218,43 @@ def profiled_traffic():
         return int(float(vals["traffic_bytes_per_launch"]))
     except (KeyError, ValueError):
         return None
+
+
+def other_workloads(dev, names=("2d_continuity_256", "3d_continuity_brain")):
+    """Matvec and forward times of the mass-preserving workloads (the continuity
+    push-forward and its derivatives), measured outside the timed region."""
+    import torch
+    from paper_1703_04446_gb300 import lgnk, synth
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for name in names:
+        ins = synth.make_inputs(name, seed=0)
+        wl = ins["workload"]
+        ctx = lgnk.Context(lgnk.Problem.from_workload(wl), device=dev)
+        dv = synth.random_velocity(wl.velocity, wl.time_nodes, 2 * min(wl.image.h), 5).astype(np.float32)
+        tv, tT, tdv = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (ins["v0"], ins["T"], dv))
+        res = torch.empty_like(tv)
+
+        def avg_ms(fn, n):
+            for _ in range(2):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / n
+
+        h_ms = avg_ms(lambda: ctx.hessvec(tv, tT, tdv, res), 10)
+        f_ms = avg_ms(lambda: ctx.forward(tv, tT), 10)
+        out[name] = {"unknowns": int(tv.numel()), "voxels": int(tT.numel()), "time_nodes": wl.time_nodes,
+                     "rk4_steps": wl.rk4_steps, "hessvec_ms": h_ms, "matvecs_per_s": 1000.0 / h_ms,
+                     "forward_ms": f_ms,
+                     "forward_voxel_steps_per_s": int(tT.numel()) * wl.rk4_steps / (f_ms * 1e-3)}
+        ctx.close()
+        del tv, tT, tdv, res
+    return out
 
 
 # ------------------------------------------------------------- CPU oracle --
@@ -364,6 +402,17 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     fwd_ms = fwd_ev[0].elapsed_time(fwd_ev[1]) / 10
     voxel_steps = int(np.prod(wl.image.m)) * wl.rk4_steps
+    # objective + gradient (SSD, J^T of the residual, regularizer) on the same problem
+    og_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(2):
+        ctx.objective(tv, tT, tR, grad=True)
+    og_ev[0].record(stream)
+    for _ in range(10):
+        ctx.objective(tv, tT, tR, grad=True)
+    og_ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    objgrad_ms = og_ev[0].elapsed_time(og_ev[1]) / 10
+    others = {} if args.no_other_workloads else other_workloads(dev)
     tts = None
     if not args.no_solve:
         torch.cuda.synchronize(dev)
@@ -405,7 +454,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "extra": {"forward_voxel_steps_per_s": voxel_steps / (fwd_ms * 1e-3), "forward_ms": fwd_ms,
-                  "time_to_solution": tts},
+                  "objective_gradient_ms": objgrad_ms, "time_to_solution": tts, "other_workloads": others},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ins)
@@ -421,6 +470,7 @@ def main():
     ap.add_argument("--max-gn", type=int, default=30)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
