@@ -133,3 +133,69 @@ def gauss_newton(prob: Problem, T, R, v0, max_gn=10, gtol=1e-3, max_pcg=50,
         g = gradient(prob, v, T, R)
     rep.update({"J": J, "D": D, "S": S, "g": float(np.sqrt(np.sum(g * g)))})
     return v, rep
+
+
+# ---------------------------------------------------------------------------
+# Multilevel continuation (Sec. 3.2, last paragraph): solve on a coarse
+# discretisation, refine the velocity and use it as the starting guess of the
+# next level.
+# ---------------------------------------------------------------------------
+
+def coarse_grid(grid, factor=2):
+    """The same box with every cell count divided by ``factor`` (cell counts must divide)."""
+    from .lagrangian import Grid
+    if any(m % factor for m in grid.m):
+        raise ValueError("cell counts must be divisible by the coarsening factor")
+    return Grid(tuple(m // factor for m in grid.m), grid.lo, grid.hi)
+
+
+def restrict_image(F: np.ndarray, grid) -> np.ndarray:
+    """Average of the 2^d fine cells that tile each coarse cell (keeps the integral
+    of the image: mean value times cell volume)."""
+    d = grid.d
+    shape = []
+    for a in reversed(range(d)):
+        shape += [grid.m[a] // 2, 2]
+    blocks = np.asarray(F, dtype=np.float64).reshape(shape)
+    return blocks.mean(axis=tuple(range(1, 2 * d, 2)))
+
+
+def prolong_velocity(vc: np.ndarray, cgrid, fgrid) -> np.ndarray:
+    """Coarse velocity interpolated (Sec. 3.1, Step 1 interpolation) at the fine
+    velocity grid's cell centres, per time node and component."""
+    from .lagrangian import cell_centres, interpolate
+    x = cell_centres(fgrid)
+    out = np.zeros((vc.shape[0], vc.shape[1]) + fgrid.shape)
+    for j in range(vc.shape[0]):
+        for c in range(vc.shape[1]):
+            out[j, c] = interpolate(vc[j, c], cgrid, x).reshape(fgrid.shape)
+    return out
+
+
+def level_problems(prob: Problem, levels: int):
+    """Problems from coarsest to finest; level l halves both grids (levels - 1 - l) times."""
+    probs = [prob]
+    for _ in range(levels - 1):
+        p = probs[0]
+        probs.insert(0, Problem(coarse_grid(p.igrid), coarse_grid(p.vgrid), K=p.K, N=p.N, model=p.model,
+                                reg=p.reg, alpha=p.alpha, gamma=p.gamma, mu=p.mu, lam=p.lam))
+    return probs
+
+
+def multilevel_gauss_newton(prob: Problem, T, R, levels, **gn):
+    """Coarse-to-fine Gauss-Newton: images restricted by averaging, each level
+    started from the prolonged solution of the coarser one (zero on the coarsest).
+    Returns (v on the finest level, list of per-level reports)."""
+    probs = level_problems(prob, levels)
+    Ts, Rs = [np.asarray(T, dtype=np.float64)], [np.asarray(R, dtype=np.float64)]
+    for l in range(levels - 1, 0, -1):
+        Ts.insert(0, restrict_image(Ts[0], probs[l].igrid))
+        Rs.insert(0, restrict_image(Rs[0], probs[l].igrid))
+    v = np.zeros(probs[0].vshape)
+    reports = []
+    for l, p in enumerate(probs):
+        if l > 0:
+            v = prolong_velocity(v, probs[l - 1].vgrid, p.vgrid)
+        v, rep = gauss_newton(p, Ts[l], Rs[l], v, **gn)
+        reports.append(rep)
+    return v, reports
