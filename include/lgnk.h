@@ -178,6 +178,33 @@ void lgnk_solve_opts_default(lgnk_solve_opts* opts);
 lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v_inout,
                        const lgnk_solve_opts* opts, lgnk_solve_report* report);
 
+/* Multilevel continuation (Sec. 3.2, last paragraph).
+ *
+ * lgnk_restrict_image: coarse image C (m/2 cells per axis, same box) = the
+ * average of the 2^d fine cells tiling each coarse cell; keeps the integral.
+ * fine->m must be even.  F[M_fine] in, C[M_fine / 2^d] out (device).
+ *
+ * lgnk_prolong_velocity: vf = the coarse velocity vc (layout [K][d][z][y][x] on
+ * `coarse`) interpolated multilinearly, zero outside the coarse grid, at the
+ * cell centres of `fine`, per time node and component.
+ *
+ * lgnk_solve_multilevel: Gauss-Newton (lgnk_solve with opts) on `levels`
+ * discretisations from the coarsest (every cell count of image and velocity
+ * divided by 2^(levels-1)) to `fine`.  Images are restricted level by level;
+ * the coarsest level starts from v = 0 and every finer level from the
+ * prolonged solution of the coarser one.  v_out[n_fine] (device) receives the
+ * finest solution; reports: NULL or `levels` entries, coarsest first.  The call
+ * allocates each level's context and buffers (within mem_budget, 0 = no bound)
+ * and frees them before it returns; it synchronises the stream.  Returns the
+ * finest level's lgnk_solve status.  All three report details through
+ * lgnk_last_error(NULL). */
+lgnk_status lgnk_restrict_image(const lgnk_grid* fine, const float* F, float* C, void* stream);
+lgnk_status lgnk_prolong_velocity(const lgnk_grid* coarse, const lgnk_grid* fine, int time_nodes,
+                                  const float* vc, float* vf, void* stream);
+lgnk_status lgnk_solve_multilevel(const lgnk_problem* fine, int levels, void* stream, size_t mem_budget,
+                                  const float* T, const float* R, float* v_out,
+                                  const lgnk_solve_opts* opts, lgnk_solve_report* reports);
+
 /* Allocation-free transport forward and SSD, for callers that must not call
  * cudaMalloc after start-up: a latency-critical loop (cudaMalloc can
  * synchronise the device and takes unbounded time) or a process whose device

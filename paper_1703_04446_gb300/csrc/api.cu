@@ -836,4 +836,175 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
     return status;
 }
 
+lgnk_status lgnk_restrict_image(const lgnk_grid* fine, const float* F, float* C, void* stream) {
+    g_create_err[0] = 0;
+    if (fine == nullptr || F == nullptr || C == nullptr || F == C) {
+        snprintf(g_create_err, sizeof(g_create_err), "fine grid, F and C must be non-NULL and distinct");
+        return LGNK_ERR_INVALID_ARG;
+    }
+    const int d = fine->d;
+    if (d != 2 && d != 3) return LGNK_ERR_INVALID_ARG;
+    if (const char* e = validate_grid(*fine, d)) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", e);
+        return LGNK_ERR_INVALID_ARG;
+    }
+    lgnk_grid cgr = *fine;
+    for (int a = 0; a < d; ++a) {
+        if (fine->m[a] % 2 != 0) {
+            snprintf(g_create_err, sizeof(g_create_err), "cell counts must be even to coarsen");
+            return LGNK_ERR_INVALID_ARG;
+        }
+        cgr.m[a] = fine->m[a] / 2;
+    }
+    const cudaError_t e = launch_restrict_image(d, F, C, make_grid(cgr), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", cudaGetErrorString(e));
+        return LGNK_ERR_CUDA;
+    }
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_prolong_velocity(const lgnk_grid* coarse, const lgnk_grid* fine, int time_nodes, const float* vc,
+                                  float* vf, void* stream) {
+    g_create_err[0] = 0;
+    if (coarse == nullptr || fine == nullptr || vc == nullptr || vf == nullptr || vc == vf || time_nodes < 1 ||
+        coarse->d != fine->d || (coarse->d != 2 && coarse->d != 3)) {
+        snprintf(g_create_err, sizeof(g_create_err), "invalid prolongation arguments");
+        return LGNK_ERR_INVALID_ARG;
+    }
+    const char* e1 = validate_grid(*coarse, coarse->d);
+    const char* e2 = validate_grid(*fine, fine->d);
+    if (e1 || e2) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", e1 ? e1 : e2);
+        return LGNK_ERR_INVALID_ARG;
+    }
+    const cudaError_t e = launch_prolong_velocity(coarse->d, vc, vf, make_grid(*coarse), make_grid(*fine),
+                                                  time_nodes * coarse->d, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", cudaGetErrorString(e));
+        return LGNK_ERR_CUDA;
+    }
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_solve_multilevel(const lgnk_problem* fine, int levels, void* stream, size_t mem_budget,
+                                  const float* T, const float* R, float* v_out, const lgnk_solve_opts* opts,
+                                  lgnk_solve_report* reports) {
+    g_create_err[0] = 0;
+    if (const char* e = validate_problem(fine)) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", e);
+        return LGNK_ERR_INVALID_ARG;
+    }
+    if (levels < 1 || levels > 8 || T == nullptr || R == nullptr || v_out == nullptr) {
+        snprintf(g_create_err, sizeof(g_create_err), "levels must be in [1, 8]; T, R, v_out non-NULL");
+        return LGNK_ERR_INVALID_ARG;
+    }
+    const int d = fine->image.d;
+    const int f = 1 << (levels - 1);
+    for (int a = 0; a < d; ++a) {
+        if (fine->image.m[a] % f != 0 || fine->velocity.m[a] % f != 0) {
+            snprintf(g_create_err, sizeof(g_create_err), "cell counts must be divisible by 2^(levels-1)");
+            return LGNK_ERR_INVALID_ARG;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // level problems, coarsest first
+    std::vector<lgnk_problem> probs(levels, *fine);
+    for (int l = 0; l < levels; ++l) {
+        const int div = 1 << (levels - 1 - l);
+        for (int a = 0; a < d; ++a) {
+            probs[l].image.m[a] = fine->image.m[a] / div;
+            probs[l].velocity.m[a] = fine->velocity.m[a] / div;
+        }
+    }
+    auto voxels = [&](const lgnk_grid& g) {
+        size_t n = 1;
+        for (int a = 0; a < d; ++a) n *= (size_t)g.m[a];
+        return n;
+    };
+    std::vector<void*> owned;
+    size_t used = 0;
+    lgnk_status status = LGNK_OK;
+    auto alloc = [&](size_t bytes, float** out) -> lgnk_status {
+        if (mem_budget != 0 && used + bytes > mem_budget) {
+            snprintf(g_create_err, sizeof(g_create_err), "multilevel buffers exceed the memory budget");
+            return LGNK_ERR_OOM;
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            snprintf(g_create_err, sizeof(g_create_err), "cudaMalloc(%zu) failed", bytes);
+            return LGNK_ERR_OOM;
+        }
+        owned.push_back(p);
+        used += bytes;
+        *out = static_cast<float*>(p);
+        return LGNK_OK;
+    };
+    auto cleanup = [&]() {
+        for (void* p : owned) cudaFree(p);
+        owned.clear();
+    };
+    // restricted images per level (the finest are the caller's)
+    std::vector<const float*> Ts(levels), Rs(levels);
+    Ts[levels - 1] = T;
+    Rs[levels - 1] = R;
+    for (int l = levels - 2; l >= 0; --l) {
+        float *tl = nullptr, *rl = nullptr;
+        const size_t nb = voxels(probs[l].image) * sizeof(float);
+        if ((status = alloc(nb, &tl)) != LGNK_OK || (status = alloc(nb, &rl)) != LGNK_OK) {
+            cleanup();
+            return status;
+        }
+        const DevGrid cg = make_grid(probs[l].image);
+        if (launch_restrict_image(d, Ts[l + 1], tl, cg, s) != cudaSuccess ||
+            launch_restrict_image(d, Rs[l + 1], rl, cg, s) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            snprintf(g_create_err, sizeof(g_create_err), "restriction launch failed");
+            return LGNK_ERR_CUDA;
+        }
+        Ts[l] = tl;
+        Rs[l] = rl;
+    }
+    float* v_prev = nullptr;
+    lgnk_status last = LGNK_OK;
+    for (int l = 0; l < levels; ++l) {
+        const size_t n = voxels(probs[l].velocity) * d * fine->time_nodes;
+        float* vl = v_out;
+        if (l < levels - 1 && (status = alloc(n * sizeof(float), &vl)) != LGNK_OK) {
+            cleanup();
+            return status;
+        }
+        cudaError_t e = cudaSuccess;
+        if (l == 0) e = cudaMemsetAsync(vl, 0, n * sizeof(float), s);
+        else e = launch_prolong_velocity(d, v_prev, vl, make_grid(probs[l - 1].velocity),
+                                          make_grid(probs[l].velocity), fine->time_nodes * d, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            snprintf(g_create_err, sizeof(g_create_err), "prolongation failed");
+            return LGNK_ERR_CUDA;
+        }
+        lgnk_ctx* ctx = nullptr;
+        const size_t left = mem_budget == 0 ? 0 : (mem_budget > used ? mem_budget - used : 1);
+        if ((status = lgnk_create(&probs[l], stream, left, &ctx)) != LGNK_OK) {
+            cleanup();
+            return status;
+        }
+        last = lgnk_solve(ctx, Ts[l], Rs[l], vl, opts, reports ? &reports[l] : nullptr);
+        if (last != LGNK_OK && last != LGNK_NOT_CONVERGED && last != LGNK_LS_FAILED) {
+            snprintf(g_create_err, sizeof(g_create_err), "level %d: %.400s", l, ctx->err);
+            lgnk_destroy(ctx);
+            cleanup();
+            return last;
+        }
+        lgnk_destroy(ctx);
+        v_prev = vl;
+    }
+    cudaStreamSynchronize(s);
+    cleanup();
+    return last;
+}
+
 }  // extern "C"

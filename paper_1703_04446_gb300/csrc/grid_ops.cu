@@ -329,6 +329,69 @@ __global__ void add_scaled_kernel(float* out, const float* x, float ax, const fl
         out[i] = fmaf(ax, x[i], ay * y[i]);
 }
 
+// ------------------------------------------------------------- multilevel --
+
+// Coarse cell = average of the 2^d fine cells that tile it (fine m = 2 coarse m).
+template <int D>
+__global__ void restrict_image_kernel(const float* __restrict__ F, float* __restrict__ C, DevGrid cg) {
+    const size_t Mc = (size_t)cg.m[0] * cg.m[1] * cg.m[2];
+    const int fm0 = 2 * cg.m[0], fm1 = 2 * cg.m[1];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < Mc; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % cg.m[0]);
+        const int y = (int)((i / cg.m[0]) % cg.m[1]);
+        const int z = (int)(i / ((size_t)cg.m[0] * cg.m[1]));
+        float s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < (1 << D); ++c) {
+            const int fx = 2 * x + (c & 1), fy = 2 * y + ((c >> 1) & 1), fz = D == 3 ? 2 * z + ((c >> 2) & 1) : 0;
+            s += F[((size_t)fz * fm1 + fy) * fm0 + fx];
+        }
+        C[i] = s * (1.0f / (1 << D));
+    }
+}
+
+// Fine velocity = coarse velocity interpolated (multilinear, zero outside the
+// coarse grid) at the fine cell centres, per time node and component.
+template <int D>
+__global__ void prolong_velocity_kernel(const float* __restrict__ vc, float* __restrict__ vf, DevGrid cg, DevGrid fg,
+                                        int blocks) {
+    const size_t Mf = (size_t)fg.m[0] * fg.m[1] * fg.m[2];
+    const size_t Mc = (size_t)cg.m[0] * cg.m[1] * cg.m[2];
+    const size_t total = Mf * blocks;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = i % Mf;
+        const size_t b = i / Mf;
+        const int fi[3] = {(int)(s % fg.m[0]), (int)((s / fg.m[0]) % fg.m[1]), (int)(s / ((size_t)fg.m[0] * fg.m[1]))};
+        int c0[3];
+        float fr[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const float x = fg.lo[a] + ((float)fi[a] + 0.5f) * fg.h[a];
+            const float xi = (x - cg.lo[a]) * cg.inv_h[a] - 0.5f;
+            const float fl = floorf(xi);
+            c0[a] = (int)fl;
+            fr[a] = xi - fl;
+        }
+        const float* src = vc + b * Mc;
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < (1 << D); ++c) {
+            float w = 1.0f;
+            int idx[3] = {0, 0, 0};
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int bit = (c >> a) & 1;
+                idx[a] = c0[a] + bit;
+                w *= bit ? fr[a] : 1.0f - fr[a];
+                in = in && idx[a] >= 0 && idx[a] < cg.m[a];
+            }
+            if (in) acc = fmaf(w, src[((size_t)idx[2] * cg.m[1] + idx[1]) * cg.m[0] + idx[0]], acc);
+        }
+        vf[b * Mf + s] = acc;
+    }
+}
+
 inline int grid_for(size_t count) {
     const size_t b = (count + kBlock - 1) / kBlock;
     return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -471,5 +534,20 @@ cudaError_t launch_axpby(float a, const float* x, float b, float* y, size_t coun
 cudaError_t launch_add_scaled(float* out, const float* x, float ax, const float* y, float ay, size_t count,
                               cudaStream_t s) {
     add_scaled_kernel<<<grid_for(count), kBlock, 0, s>>>(out, x, ax, y, ay, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_image(int d, const float* F, float* C, const DevGrid& cg, cudaStream_t s) {
+    const size_t Mc = (size_t)cg.m[0] * cg.m[1] * cg.m[2];
+    if (d == 3) restrict_image_kernel<3><<<grid_for(Mc), kBlock, 0, s>>>(F, C, cg);
+    else restrict_image_kernel<2><<<grid_for(Mc), kBlock, 0, s>>>(F, C, cg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_velocity(int d, const float* vc, float* vf, const DevGrid& cg, const DevGrid& fg,
+                                    int blocks, cudaStream_t s) {
+    const size_t total = (size_t)fg.m[0] * fg.m[1] * fg.m[2] * blocks;
+    if (d == 3) prolong_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>(vc, vf, cg, fg, blocks);
+    else prolong_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>(vc, vf, cg, fg, blocks);
     return cudaGetLastError();
 }

@@ -113,6 +113,12 @@ cudaError_t launch_axpby(float a, const float* x, float b, float* y, size_t coun
 cudaError_t launch_add_scaled(float* out, const float* x, float ax, const float* y, float ay, size_t count,
                               cudaStream_t s);
 
+// multilevel: 2^d-cell averaging onto the coarse grid cg; multilinear
+// prolongation of `blocks` scalar fields from grid cg to grid fg
+cudaError_t launch_restrict_image(int d, const float* F, float* C, const DevGrid& cg, cudaStream_t s);
+cudaError_t launch_prolong_velocity(int d, const float* vc, float* vf, const DevGrid& cg, const DevGrid& fg,
+                                    int blocks, cudaStream_t s);
+
 // api.cu helpers for entry points that run without a context
 const char* lgnk_internal_validate(const lgnk_problem* p);  // NULL if valid, else why not
 DevGrid lgnk_internal_grid(const lgnk_grid& g);

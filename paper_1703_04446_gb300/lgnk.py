@@ -14,6 +14,7 @@ import ctypes
 import os
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 PKG = os.path.dirname(os.path.abspath(__file__))
@@ -81,6 +82,12 @@ EXPORTS = {
     "lgnk_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "lgnk_forward_transport_static": (ctypes.c_int, [ctypes.POINTER(_Problem)] + [ctypes.c_void_p] * 6),
+    "lgnk_restrict_image": (ctypes.c_int, [ctypes.POINTER(_Grid)] + [ctypes.c_void_p] * 3),
+    "lgnk_prolong_velocity": (ctypes.c_int, [ctypes.POINTER(_Grid), ctypes.POINTER(_Grid), ctypes.c_int]
+                              + [ctypes.c_void_p] * 3),
+    "lgnk_solve_multilevel": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.POINTER(_SolveOpts), ctypes.c_void_p]),
     "lgnk_solve_opts_default": (None, [ctypes.POINTER(_SolveOpts)]),
     "lgnk_solve": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.POINTER(_SolveOpts),
                                                          ctypes.POINTER(_SolveReport)]),
@@ -377,6 +384,84 @@ def lgnk_solve(ctx: Context, T, R, v0=None, **opts):
     if st not in (0, 6, 7):
         raise LgnkError(st, ctx.lib.lgnk_last_error(ctx.handle).decode())
     return v, report
+
+
+def _grid_c(m, lo, hi):
+    g = _Grid()
+    g.d = len(m)
+    for a in range(3):
+        g.m[a] = int(m[a]) if a < len(m) else 1
+        g.lo[a] = float(lo[a]) if a < len(m) else 0.0
+        g.hi[a] = float(hi[a]) if a < len(m) else 1.0
+    return g
+
+
+def _raise_free(lib, st):
+    if st != 0:
+        raise LgnkError(st, lib.lgnk_last_error(None).decode())
+
+
+def lgnk_restrict_image(F, m, lo=None, hi=None):
+    """Average of the 2^d fine cells tiling each coarse cell (m: fine cell counts, x first)."""
+    lib = load_library()
+    d = len(m)
+    lo = lo or (0.0,) * d
+    hi = hi or (1.0,) * d
+    if F.dtype != torch.float32 or not F.is_cuda or not F.is_contiguous() or F.numel() != int(np.prod(m)):
+        raise ValueError("F must be a contiguous float32 CUDA tensor with prod(m) elements")
+    C = torch.empty(tuple(reversed([a // 2 for a in m])), device=F.device, dtype=torch.float32)
+    g = _grid_c(m, lo, hi)
+    _raise_free(lib, lib.lgnk_restrict_image(ctypes.byref(g), _ptr(F), _ptr(C),
+                                             ctypes.c_void_p(torch.cuda.current_stream(F.device).cuda_stream)))
+    return C
+
+
+def lgnk_prolong_velocity(vc, coarse_m, fine_m, lo=None, hi=None):
+    """Multilinear interpolation of the coarse velocity [K][d][...] at the fine cell centres."""
+    lib = load_library()
+    d = len(coarse_m)
+    lo = lo or (0.0,) * d
+    hi = hi or (1.0,) * d
+    K = vc.shape[0]
+    if vc.dtype != torch.float32 or not vc.is_cuda or not vc.is_contiguous():
+        raise ValueError("vc must be a contiguous float32 CUDA tensor")
+    vf = torch.empty((K, d) + tuple(reversed(fine_m)), device=vc.device, dtype=torch.float32)
+    cg, fg = _grid_c(coarse_m, lo, hi), _grid_c(fine_m, lo, hi)
+    _raise_free(lib, lib.lgnk_prolong_velocity(ctypes.byref(cg), ctypes.byref(fg), K, _ptr(vc), _ptr(vf),
+                                               ctypes.c_void_p(torch.cuda.current_stream(vc.device).cuda_stream)))
+    return vf
+
+
+def lgnk_solve_multilevel(problem: Problem, T, R, levels, mem_budget=0, **opts):
+    """Coarse-to-fine Gauss-Newton (Sec. 3.2).  Returns (v on the finest level,
+    list of per-level report dicts, coarsest first)."""
+    lib = load_library()
+    dev = T.device
+    for t, name in ((T, "T"), (R, "R")):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or \
+                t.numel() != int(torch.Size(problem.image_shape).numel()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of the image shape")
+    v = torch.empty(problem.velocity_shape, device=dev, dtype=torch.float32)
+    o = _SolveOpts()
+    lib.lgnk_solve_opts_default(ctypes.byref(o))
+    for k, val in opts.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown solve option {k}")
+        setattr(o, k, type(getattr(o, k))(val))
+    reps = (_SolveReport * levels)()
+    pc = problem.to_c()
+    st = lib.lgnk_solve_multilevel(ctypes.byref(pc), int(levels),
+                                   ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream),
+                                   ctypes.c_size_t(mem_budget), _ptr(T), _ptr(R), _ptr(v), ctypes.byref(o),
+                                   ctypes.cast(reps, ctypes.c_void_p))
+    if st not in (0, 6, 7):
+        raise LgnkError(st, lib.lgnk_last_error(None).decode())
+    out = []
+    for r in reps:
+        d = {f: getattr(r, f) for f, _ in _SolveReport._fields_}
+        d["status_name"] = STATUS.get(d["status"], str(d["status"]))
+        out.append(d)
+    return v, out
 
 
 class LagrangianForward(torch.autograd.Function):
