@@ -128,6 +128,15 @@ lgnk_status lgnk_hessvec(lgnk_ctx* ctx, const float* v, const float* T, const fl
  * P positive definite (elastic uses its mu-Laplacian part).  r[n] in; z[n] out. */
 lgnk_status lgnk_precond(lgnk_ctx* ctx, const float* r, float* z);
 
+/* Jacobian determinant det grad y of the map the velocity generates (the paper
+ * monitors its range to check that the transformation stays diffeomorphic,
+ * Sec. 2.1, Sec. 4): y = y(v, x_c, 1, 0) for transport, y(v, x_c, 0, 1) for
+ * continuity, differentiated at the cell centres with central differences
+ * (one-sided at the ends).  v[n], T[M] in (T as for lgnk_forward); det: NULL or
+ * device [M]; det_min / det_max: host doubles (may be NULL).  Synchronises. */
+lgnk_status lgnk_jacobian_determinant(lgnk_ctx* ctx, const float* v, const float* T, float* det,
+                                      double* det_min, double* det_max);
+
 /* FP64 inner product of two device float arrays of length count; host result.
  * Synchronises the stream. */
 lgnk_status lgnk_dot(lgnk_ctx* ctx, const float* a, const float* b, size_t count, double* out);

@@ -303,3 +303,21 @@ def jtvp(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, r):
         _, gr = interpolate(r, igrid, y, gradient=True)
         lam = gr * np.asarray(T, dtype=np.float64).reshape(-1)
     return characteristics_adjoint(v, vgrid, hist, N, direction, lam)
+
+
+def jacobian_determinant(y: np.ndarray, grid: Grid) -> np.ndarray:
+    """det grad y of a map sampled at the cell centres (y: (d, M) end points),
+    with central differences inside and one-sided differences at the ends
+    (numpy.gradient, edge order 1).  The paper monitors it to check that the
+    discrete transformation stays diffeomorphic (Sec. 4)."""
+    d = grid.d
+    comps = [y[a].reshape(grid.shape) for a in range(d)]
+    J = np.zeros((d, d) + grid.shape)
+    for a in range(d):
+        for b in range(d):
+            J[a, b] = np.gradient(comps[a], grid.h[b], axis=d - 1 - b, edge_order=1)
+    if d == 2:
+        return J[0, 0] * J[1, 1] - J[0, 1] * J[1, 0]
+    return (J[0, 0] * (J[1, 1] * J[2, 2] - J[1, 2] * J[2, 1])
+            - J[0, 1] * (J[1, 0] * J[2, 2] - J[1, 2] * J[2, 0])
+            + J[0, 2] * (J[1, 0] * J[2, 1] - J[1, 1] * J[2, 0]))

@@ -43,6 +43,7 @@ struct lgnk_ctx {
     double* hres = nullptr;       // pinned host mirror of dres
     float* sv[7] = {nullptr};
     bool have_solve = false;
+    float* ybuf = nullptr;        // end points [d][M] for lgnk_jacobian_determinant
     std::vector<void*> allocs;
     // profiling: CUDA events around every tracing-kernel launch, kernel counter
     bool prof = false;
@@ -547,7 +548,7 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     for (int a = 0; a < d; ++a)
         if ((s = dalloc(ctx, (size_t)ctx->vg.m[a] * ctx->vg.m[a], &ctx->Cm[a])) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, ctx->Mv, &ctx->inv_eig)) != LGNK_OK) return fail(s);
-    ctx->npartial = ctx->trace_blocks > 1024 ? ctx->trace_blocks : 1024;
+    ctx->npartial = ctx->trace_blocks > 1280 ? ctx->trace_blocks : 1280;  // >= 2 x 608 min/max partials
     if ((s = dalloc(ctx, (size_t)ctx->npartial, &ctx->partial)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 8, &ctx->dres)) != LGNK_OK) return fail(s);
     if (cudaMallocHost((void**)&ctx->hres, 8 * sizeof(double)) != cudaSuccess) {
@@ -666,6 +667,23 @@ lgnk_status lgnk_hessvec(lgnk_ctx* ctx, const float* v, const float* T, const fl
     TRY(pack_v(ctx, v, ctx->Vp));
     if (ctx->prob.model == LGNK_TRANSPORT) TRY(pack_T(ctx, T));
     return hessvec_packed(ctx, T, dv, Hdv);
+}
+
+lgnk_status lgnk_jacobian_determinant(lgnk_ctx* ctx, const float* v, const float* T, float* det, double* det_min,
+                                      double* det_max) {
+    CHECK_CTX();
+    REQUIRE(v && T, "v and T must be non-NULL");
+    REQUIRE(distinct(det, {v, T}), "det must not alias the inputs");
+    if (ctx->ybuf == nullptr) TRY(dalloc(ctx, ctx->M * ctx->d, &ctx->ybuf));
+    TRY(pack_v(ctx, v, ctx->Vp));
+    if (ctx->prob.model == LGNK_TRANSPORT) TRY(pack_T(ctx, T));
+    TRY(forward_packed(ctx, T, ctx->itmp, ctx->ybuf));
+    KL(launch_jacobian_det(ctx->d, ctx->ybuf, det, ctx->ig, ctx->partial, ctx->dres + 4, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hres + 4, ctx->dres + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (det_min) *det_min = ctx->hres[4];
+    if (det_max) *det_max = ctx->hres[5];
+    return LGNK_OK;
 }
 
 lgnk_status lgnk_precond(lgnk_ctx* ctx, const float* r, float* z) {

@@ -392,6 +392,82 @@ __global__ void prolong_velocity_kernel(const float* __restrict__ vc, float* __r
     }
 }
 
+// ------------------------------------------------- Jacobian determinant --
+
+__device__ __forceinline__ void block_minmax(double& lo, double& hi) {
+    __shared__ double slo[kBlock / 32], shi[kBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        slo[warp] = lo;
+        shi[warp] = hi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        lo = lane < kBlock / 32 ? slo[lane] : INFINITY;
+        hi = lane < kBlock / 32 ? shi[lane] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+        }
+    }
+}
+
+// det grad y at the cell centres from the end points y [d][M]: central
+// differences inside, one-sided at the ends; block min/max into partials.
+template <int D>
+__global__ void jacobian_det_kernel(const float* __restrict__ y, float* det, DevGrid g, double* pmin, double* pmax) {
+    const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
+    double lo = INFINITY, hi = -INFINITY;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+        const int c[3] = {(int)(i % g.m[0]), (int)((i / g.m[0]) % g.m[1]), (int)(i / ((size_t)g.m[0] * g.m[1]))};
+        double J[3][3];
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            const size_t up = c[b] < g.m[b] - 1 ? i + stride[b] : i;
+            const size_t dn = c[b] > 0 ? i - stride[b] : i;
+            const double span = (double)g.h[b] * (double)((up != i) + (dn != i));
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float* ya = y + (size_t)a * M;
+                J[a][b] = span > 0.0 ? ((double)ya[up] - (double)ya[dn]) / span : (a == b ? 1.0 : 0.0);
+            }
+        }
+        double dt;
+        if (D == 2) dt = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        else
+            dt = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (det != nullptr) det[i] = (float)dt;
+        lo = fmin(lo, dt);
+        hi = fmax(hi, dt);
+    }
+    block_minmax(lo, hi);
+    if (threadIdx.x == 0) {
+        pmin[blockIdx.x] = lo;
+        pmax[blockIdx.x] = hi;
+    }
+}
+
+__global__ void minmax_final_kernel(const double* pmin, const double* pmax, int count, double* out) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        lo = fmin(lo, pmin[i]);
+        hi = fmax(hi, pmax[i]);
+    }
+    block_minmax(lo, hi);
+    if (threadIdx.x == 0) {
+        out[0] = lo;
+        out[1] = hi;
+    }
+}
+
 inline int grid_for(size_t count) {
     const size_t b = (count + kBlock - 1) / kBlock;
     return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -549,5 +625,20 @@ cudaError_t launch_prolong_velocity(int d, const float* vc, float* vf, const Dev
     const size_t total = (size_t)fg.m[0] * fg.m[1] * fg.m[2] * blocks;
     if (d == 3) prolong_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>(vc, vf, cg, fg, blocks);
     else prolong_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>(vc, vf, cg, fg, blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian_det(int d, const float* y, float* det, const DevGrid& g, double* partial, double* out,
+                                cudaStream_t s) {
+    const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const int nb = residual_blocks(g, d);
+    double* pmin = partial;
+    double* pmax = partial + nb;
+    if (d == 3) jacobian_det_kernel<3><<<nb, kBlock, 0, s>>>(y, det, g, pmin, pmax);
+    else jacobian_det_kernel<2><<<nb, kBlock, 0, s>>>(y, det, g, pmin, pmax);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    (void)M;
+    minmax_final_kernel<<<1, kBlock, 0, s>>>(pmin, pmax, nb, out);
     return cudaGetLastError();
 }

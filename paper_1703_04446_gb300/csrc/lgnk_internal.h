@@ -119,6 +119,11 @@ cudaError_t launch_restrict_image(int d, const float* F, float* C, const DevGrid
 cudaError_t launch_prolong_velocity(int d, const float* vc, float* vf, const DevGrid& cg, const DevGrid& fg,
                                     int blocks, cudaStream_t s);
 
+// det grad y of end points y [d][M] (det may be NULL); min, max -> out[0], out[1];
+// partial needs 2 * residual_blocks(g, d) doubles
+cudaError_t launch_jacobian_det(int d, const float* y, float* det, const DevGrid& g, double* partial, double* out,
+                                cudaStream_t s);
+
 // api.cu helpers for entry points that run without a context
 const char* lgnk_internal_validate(const lgnk_problem* p);  // NULL if valid, else why not
 DevGrid lgnk_internal_grid(const lgnk_grid& g);

@@ -77,6 +77,7 @@ EXPORTS = {
                        + [ctypes.c_void_p]),
     "lgnk_hessvec": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "lgnk_precond": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "lgnk_jacobian_determinant": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.POINTER(ctypes.c_double)] * 2),
     "lgnk_dot": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
     "lgnk_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lgnk_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -270,6 +271,9 @@ class Context:
     def precond(self, r):
         return lgnk_precond(self, r)
 
+    def jacobian_determinant(self, v, T, field=True):
+        return lgnk_jacobian_determinant(self, v, T, field)
+
     def dot(self, a, b):
         return lgnk_dot(self, a, b)
 
@@ -351,6 +355,17 @@ def lgnk_precond(ctx: Context, r):
     ctx._stream()
     ctx._check(ctx.lib.lgnk_precond(ctx.handle, _ptr(r), _ptr(z)))
     return z
+
+
+def lgnk_jacobian_determinant(ctx: Context, v, T, field=True):
+    """(det grad y field or None, min, max) of the map generated by v."""
+    ctx._vel(v, "v"), ctx._img(T, "T")
+    det = ctx._new_img() if field else None
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    ctx._stream()
+    ctx._check(ctx.lib.lgnk_jacobian_determinant(ctx.handle, _ptr(v), _ptr(T), _ptr(det), ctypes.byref(lo),
+                                                 ctypes.byref(hi)))
+    return det, lo.value, hi.value
 
 
 def lgnk_dot(ctx: Context, a, b):

@@ -199,3 +199,17 @@ def test_regularizer_operator_through_hessvec_at_zero_image():
         H = ctx.hessvec(t["v"], torch.zeros_like(t["T"]), t["dv"])
         ref = op.alpha * reg_operator(op, a["dv"].astype(np.float64)) + op.gamma * a["dv"].astype(np.float64)
         assert rel(_np(H), ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["2d_transport_ragged_K3", "3d_transport_ragged", "3d_continuity_K2"])
+def test_jacobian_determinant(name):
+    """det grad y of the generated map against the oracle's finite differences of
+    its own end points (Sec. 4 monitors its range)."""
+    ctx, t = _gpu(name)
+    op, gp, a = make_case(name)
+    det, lo, hi = ctx.jacobian_determinant(t["v"], t["T"])
+    ref = L.jacobian_determinant(_oracle(name)["y"], op.igrid)
+    got = det.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    assert abs(lo - ref.min()) <= 1e-4 * abs(ref.min()) and abs(hi - ref.max()) <= 1e-4 * abs(ref.max())
+    assert abs(lo - got.min()) <= 1e-6 * abs(lo) and abs(hi - got.max()) <= 1e-6 * abs(hi)

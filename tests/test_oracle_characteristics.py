@@ -184,3 +184,25 @@ def test_transport_and_continuity_are_adjoint_for_fixed_points():
     lhs = np.sum(L.scatter(T, ig, y) * R)
     rhs = np.sum(T * L.interpolate(R, ig, y))
     assert abs(lhs - rhs) < 1e-12 * (1 + abs(lhs))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_jacobian_determinant_of_affine_maps(d):
+    """Finite differences are exact on affine maps: det grad (A x + b) = det A,
+    also at the one-sided ends; the identity has determinant 1."""
+    g = L.Grid((7, 6, 5)[:d], hi=(1.0, 1.4, 0.8)[:d])
+    x = L.cell_centres(g)
+    A = np.eye(d) + 0.3 * np.random.default_rng(3).normal(size=(d, d))
+    y = A @ x + 0.2
+    np.testing.assert_allclose(L.jacobian_determinant(y, g), np.linalg.det(A), rtol=1e-12)
+    np.testing.assert_allclose(L.jacobian_determinant(x, g), 1.0, rtol=1e-12)
+
+
+def test_jacobian_determinant_of_rotation_flow_is_one():
+    """A rigid rotation preserves volume: det grad y = 1 up to RK4 error."""
+    vg = L.Grid((20, 20))
+    x0 = np.array([0.5, 0.5])
+    v = _vel_from(_rotation(2, 1.0, x0), vg, 1)
+    ig = L.Grid((10, 10), lo=(0.3, 0.3), hi=(0.7, 0.7))
+    y, _, _ = L.characteristics(v, vg, L.cell_centres(ig), 16, -1)
+    np.testing.assert_allclose(L.jacobian_determinant(y, ig), 1.0, atol=1e-6)
