@@ -16,7 +16,10 @@ lagrangian  interpolation I(v, y, t), RK4 characteristics with the forward-mode
             (Eqs. 7-8), their J and J^T products.
 objective   SSD (Eq. 10), regularizers (Sec. 2.1), objective, gradient,
             Gauss-Newton Hessian (Sec. 3.2).
-solver      spectral (DCT) preconditioner, PCG, Armijo, Gauss-Newton (Eq. 11).
+solver      spectral (DCT) preconditioner, PCG, Armijo, Gauss-Newton (Eq. 11),
+            multilevel continuation (Sec. 3.2).
+warmstart   the learned warm-start network (an addition, not in the paper) in
+            torch CPU FP64; imported on its own (needs torch).
 
 Parity status: every function is pinned by a test against closed forms,
 invariants, library routines or brute force, except the elastic regularizer

@@ -262,3 +262,35 @@ def make_inputs(name: str, seed: int = 0, dtype=np.float32):
         "R": np.ascontiguousarray(R, dtype=dtype),
         "v0": np.ascontiguousarray(v0, dtype=dtype),
     }
+
+
+def warmstart_init(c: int, seed: int):
+    """Seeded He-normal initial parameters (zero biases) of the warm-start
+    encoder-decoder with c base channels, as one flat float32 vector in the
+    layer order e0, e1, e2, e3, d2, d1, out (W [c_out][c_in][3][3], then b)."""
+    shapes = [(2, c), (c, 2 * c), (2 * c, 4 * c), (4 * c, 8 * c), (8 * c, 4 * c), (4 * c, 2 * c), (2 * c, 2)]
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, co in shapes:
+        out.append(rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), size=co * ci * 9))
+        out.append(np.zeros(co))
+    return np.concatenate(out).astype(np.float32)
+
+
+def prior_velocity(g: GridSpec, alpha: float, max_disp: float, seed: int, eps: float = 1e-3):
+    """Stationary velocity (1, d, *g.shape) drawn from the regularizer prior:
+    white Gaussian noise filtered in Fourier space by 1 / (alpha |k|^2 + eps)
+    (the inverse of a diffusion operator), windowed to vanish on the boundary
+    and scaled to a maximum magnitude of max_disp."""
+    rng = np.random.default_rng(seed)
+    coords = centres(g)
+    freqs = np.meshgrid(*[np.fft.fftfreq(n, d=h) for n, h in zip(reversed(g.m), reversed(g.h))], indexing="ij")
+    k2 = sum((2 * np.pi * f) ** 2 for f in freqs)
+    filt = 1.0 / (alpha * k2 + eps)
+    comps = []
+    for _ in range(g.d):
+        noise = rng.normal(size=g.shape)
+        comps.append(np.real(np.fft.ifftn(np.fft.fftn(noise) * filt)))
+    w = _window(coords, g.lo, g.hi)
+    comps = _scale_to([c * w for c in comps], max_disp)
+    return np.stack(comps)[None].astype(np.float32)
