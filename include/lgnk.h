@@ -161,6 +161,7 @@ typedef struct {
     int max_ls;           /* Armijo halvings (default 10)                          */
     int precond;          /* 1 = spectral preconditioner, 0 = none                 */
     int verbosity;        /* 0 silent, 1 one line per GN iteration on stderr       */
+    double gn_grad_atol;  /* also stop when |g| <= atol (default 0: off)           */
 } lgnk_solve_opts;
 
 typedef struct {
@@ -238,6 +239,48 @@ lgnk_status lgnk_solve_multilevel(const lgnk_problem* fine, int levels, void* st
  * lgnk_last_error(NULL).  Allocates nothing. */
 lgnk_status lgnk_forward_transport_static(const lgnk_problem* prob, const float* v, const float* T,
                                           const float* R, float* u1, double* D, void* stream);
+
+/* Learned warm start.  The paper starts every Gauss-Newton solve of Eq. 11 from
+ * v = 0 (or, with continuation, from a coarser level); this network is an
+ * addition with no counterpart there: it predicts a starting velocity from the
+ * image pair, and the solve then corrects it (the optimality conditions are
+ * unchanged, only the initial iterate differs).  2D, stationary velocity.
+ *
+ * Network for m x m images (m a multiple of 8), c base channels, 3 x 3
+ * convolutions with zero padding 1:
+ *   e0 = relu(conv(x = [T, R], 2 -> c))        e1 = relu(conv_s2(e0, c -> 2c))
+ *   e2 = relu(conv_s2(e1, 2c -> 4c))           e3 = relu(conv_s2(e2, 4c -> 8c))
+ *   d2 = relu(conv(up2(e3), 8c -> 4c)) + e2    d1 = relu(conv(up2(d2), 4c -> 2c)) + e1
+ *   v  = scale conv(d1, 2c -> 2)               (m/2 x m/2, two components)
+ * (s2: stride 2; up2: nearest-neighbour doubling).  Convolutions use the
+ * weights rounded to bfloat16; activations and accumulation are FP32.
+ * Parameters: one flat FP32 vector, per layer in the order above W[co][ci][3][3]
+ * then b[co].  Loss: 1/2 mean((v - v_target)^2) / scale^2; training: Adam
+ * (beta 0.9, 0.999, eps 1e-8) on FP32 master weights.
+ *
+ * Layouts (device, contiguous): T, R [B][m][m]; v, v_target [B][2][m/2][m/2]
+ * (component-major, the velocity layout of lgnk_forward for K = 1).
+ * lgnk_ws_create: max_batch bounds B of every later call; scale > 0; stream as
+ * in lgnk_create.  The network owns its device buffers (parameters, Adam
+ * moments, activations for max_batch) and frees them in lgnk_ws_destroy.
+ * Parameters start at zero: load them with lgnk_ws_set_params (device [P],
+ * P = lgnk_ws_num_params), which also resets Adam.  lgnk_ws_train_step runs
+ * forward, backward and one Adam step with learning rate lr; loss: NULL or a
+ * host double receiving the loss before the step (then the call synchronises
+ * the stream).  lgnk_ws_get_grads copies the gradient of the last train step.
+ * Errors: the status, with detail from lgnk_ws_last_error. */
+typedef struct lgnk_ws lgnk_ws;
+lgnk_status lgnk_ws_create(int image_m, int base_channels, int max_batch, float scale, void* stream,
+                           lgnk_ws** out);
+void lgnk_ws_destroy(lgnk_ws* ws);
+size_t lgnk_ws_num_params(const lgnk_ws* ws);
+const char* lgnk_ws_last_error(const lgnk_ws* ws);
+lgnk_status lgnk_ws_set_params(lgnk_ws* ws, const float* params);
+lgnk_status lgnk_ws_get_params(lgnk_ws* ws, float* params);
+lgnk_status lgnk_ws_get_grads(lgnk_ws* ws, float* grads);
+lgnk_status lgnk_ws_predict(lgnk_ws* ws, int batch, const float* T, const float* R, float* v);
+lgnk_status lgnk_ws_train_step(lgnk_ws* ws, int batch, const float* T, const float* R, const float* v_target,
+                               float lr, double* loss);
 
 #ifdef __cplusplus
 }

@@ -104,7 +104,7 @@ def loss_and_grad(params, T, R, v_target, c: int, scale: float):
     t = torch.as_tensor(v_target, dtype=torch.float64)
     loss = 0.5 * torch.mean((v - t) ** 2) / scale ** 2
     loss.backward()
-    return float(loss), p.grad.detach().numpy(), v.detach().numpy()
+    return float(loss.detach()), p.grad.detach().numpy(), v.detach().numpy()
 
 
 def adam_step(params, grad, m, s, step: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):

@@ -737,6 +737,7 @@ void lgnk_solve_opts_default(lgnk_solve_opts* o) {
     o->max_ls = 10;
     o->precond = 1;
     o->verbosity = 0;
+    o->gn_grad_atol = 0.0;
 }
 
 lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts* opts_in,
@@ -747,7 +748,8 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
     lgnk_solve_opts o;
     lgnk_solve_opts_default(&o);
     if (opts_in) o = *opts_in;
-    REQUIRE(o.max_gn >= 0 && o.max_pcg >= 1 && o.max_ls >= 1 && o.pcg_rtol > 0.0 && o.gn_grad_rtol >= 0.0,
+    REQUIRE(o.max_gn >= 0 && o.max_pcg >= 1 && o.max_ls >= 1 && o.pcg_rtol > 0.0 && o.gn_grad_rtol >= 0.0 &&
+                o.gn_grad_atol >= 0.0,
             "invalid solve options");
     const auto t_start = std::chrono::steady_clock::now();
     if (!ctx->have_solve) {
@@ -774,7 +776,7 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
     lgnk_status status = LGNK_NOT_CONVERGED;
     double gn = g0;
     for (int it = 0; it < o.max_gn; ++it) {
-        if (gn <= o.gn_grad_rtol * g0) {
+        if (gn <= o.gn_grad_rtol * g0 || gn <= o.gn_grad_atol) {
             status = LGNK_OK;
             break;
         }
@@ -842,7 +844,7 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             fprintf(stderr, "lgnk GN %3d  J %.6e  D %.6e  S %.6e  |g|/|g0| %.3e  pcg %d  mu %.3g\n", it + 1, J, D,
                     S, gn / g0, pit, mu);
     }
-    if (status == LGNK_NOT_CONVERGED && gn <= o.gn_grad_rtol * g0) status = LGNK_OK;
+    if (status == LGNK_NOT_CONVERGED && (gn <= o.gn_grad_rtol * g0 || gn <= o.gn_grad_atol)) status = LGNK_OK;
     CK(cudaStreamSynchronize(s));
     rep.J = J;
     rep.D = D;

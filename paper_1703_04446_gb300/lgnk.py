@@ -51,7 +51,7 @@ class _Problem(ctypes.Structure):
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("max_gn", ctypes.c_int), ("gn_grad_rtol", ctypes.c_double), ("max_pcg", ctypes.c_int),
                 ("pcg_rtol", ctypes.c_double), ("armijo_c", ctypes.c_double), ("max_ls", ctypes.c_int),
-                ("precond", ctypes.c_int), ("verbosity", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("verbosity", ctypes.c_int), ("gn_grad_atol", ctypes.c_double)]
 
 
 class _SolveReport(ctypes.Structure):
@@ -92,6 +92,17 @@ EXPORTS = {
     "lgnk_solve_opts_default": (None, [ctypes.POINTER(_SolveOpts)]),
     "lgnk_solve": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.POINTER(_SolveOpts),
                                                          ctypes.POINTER(_SolveReport)]),
+    "lgnk_ws_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "lgnk_ws_destroy": (None, [ctypes.c_void_p]),
+    "lgnk_ws_num_params": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "lgnk_ws_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "lgnk_ws_set_params": (ctypes.c_int, [ctypes.c_void_p] * 2),
+    "lgnk_ws_get_params": (ctypes.c_int, [ctypes.c_void_p] * 2),
+    "lgnk_ws_get_grads": (ctypes.c_int, [ctypes.c_void_p] * 2),
+    "lgnk_ws_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3),
+    "lgnk_ws_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
+                           + [ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -477,6 +488,86 @@ def lgnk_solve_multilevel(problem: Problem, T, R, levels, mem_budget=0, **opts):
         d["status_name"] = STATUS.get(d["status"], str(d["status"]))
         out.append(d)
     return v, out
+
+
+class WarmStart:
+    """The learned warm-start network (lgnk_ws_*): predicts a stationary 2D
+    starting velocity [B][2][m/2][m/2] from image pairs T, R [B][m][m]."""
+
+    def __init__(self, image_m: int, base_channels: int, max_batch: int, scale: float, device=None):
+        self.lib = load_library()
+        self.m, self.c, self.max_batch, self.scale = int(image_m), int(base_channels), int(max_batch), float(scale)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.lgnk_ws_create(self.m, self.c, self.max_batch, ctypes.c_float(self.scale),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                         ctypes.byref(handle))
+        if st != 0:
+            raise LgnkError(st, "lgnk_ws_create rejected its arguments or could not allocate")
+        self.handle = handle
+        self.num_params = int(self.lib.lgnk_ws_num_params(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.lgnk_ws_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise LgnkError(st, self.lib.lgnk_ws_last_error(self.handle).decode())
+
+    def _t(self, t, numel, name):
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != torch.float32 \
+                or not t.is_contiguous() or t.numel() != numel:
+            raise ValueError(f"{name} must be a contiguous float32 tensor on {self.device} with {numel} elements")
+        return _ptr(t)
+
+    def _pair(self, T, R):
+        if T.dim() == 2:
+            T, R = T[None], R[None]
+        B = T.shape[0]
+        if B < 1 or B > self.max_batch:
+            raise ValueError(f"batch {B} outside [1, {self.max_batch}]")
+        n = B * self.m * self.m
+        return B, self._t(T, n, "T"), self._t(R, n, "R")
+
+    def set_params(self, params):
+        p = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
+        self._check(self.lib.lgnk_ws_set_params(self.handle, self._t(p, self.num_params, "params")))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    def params(self):
+        out = torch.empty(self.num_params, device=self.device, dtype=torch.float32)
+        self._check(self.lib.lgnk_ws_get_params(self.handle, _ptr(out)))
+        return out
+
+    def grads(self):
+        out = torch.empty(self.num_params, device=self.device, dtype=torch.float32)
+        self._check(self.lib.lgnk_ws_get_grads(self.handle, _ptr(out)))
+        return out
+
+    def predict(self, T, R, out=None):
+        B, pT, pR = self._pair(T, R)
+        h = self.m // 2
+        v = out if out is not None else torch.empty((B, 2, h, h), device=self.device, dtype=torch.float32)
+        self._check(self.lib.lgnk_ws_predict(self.handle, B, pT, pR, self._t(v, B * 2 * h * h, "out")))
+        return v
+
+    def train_step(self, T, R, v_target, lr: float, return_loss=True):
+        B, pT, pR = self._pair(T, R)
+        h = self.m // 2
+        loss = ctypes.c_double()
+        self._check(self.lib.lgnk_ws_train_step(self.handle, B, pT, pR, self._t(v_target, B * 2 * h * h, "v_target"),
+                                                ctypes.c_float(lr), ctypes.byref(loss) if return_loss else None))
+        return loss.value if return_loss else None
 
 
 class LagrangianForward(torch.autograd.Function):

@@ -34,7 +34,7 @@ import numpy as np
 __all__ = [
     "GridSpec", "Workload", "WORKLOADS", "centres", "gaussian_blobs",
     "smooth_field", "ellipsoid_phantom", "shell_phantom", "make_inputs",
-    "random_velocity",
+    "random_velocity", "prior_velocity", "warmstart_init", "warmstart_pair",
 ]
 
 
@@ -93,7 +93,13 @@ WORKLOADS = {
         "3d_continuity_brain", _box((192, 224, 160), hi=(1.2, 1.4, 1.0)),
         _box((96, 112, 80), hi=(1.2, 1.4, 1.0)), 9, 16,
         "continuity", "diffusion", 1e-3, 0.0),
+    # image pairs of the learned warm start (128^2 images, stationary 64^2 velocity)
+    "2d_warmstart_128": Workload(
+        "2d_warmstart_128", _box((128, 128)), _box((64, 64)), 1, 4,
+        "transport", "diffusion", 1e-2, 0.0),
 }
+
+WARMSTART_MAX_DISP_PX = 10.0
 
 
 def centres(g: GridSpec):
@@ -253,6 +259,9 @@ def make_inputs(name: str, seed: int = 0, dtype=np.float32):
         mt, mr = T.sum() * cell, R.sum() * cell
         T, R = T / mt, R / mr
         vamp = 6 * h
+    elif name == "2d_warmstart_128":
+        T, v_true = warmstart_pair(0, seed)
+        return {"workload": wl, "T": T.astype(dtype), "R": None, "v0": v_true.astype(dtype)}
     else:
         raise KeyError(name)
     v0 = random_velocity(wl.velocity, wl.time_nodes, vamp, seed + 7)
@@ -275,6 +284,22 @@ def warmstart_init(c: int, seed: int):
         out.append(rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), size=co * ci * 9))
         out.append(np.zeros(co))
     return np.concatenate(out).astype(np.float32)
+
+
+def warmstart_pair(index: int, seed: int = 0):
+    """Template and true velocity of image pair `index` for the learned warm
+    start: T = 4 to 9 random Gaussian blobs on the 128^2 grid; v drawn from the
+    diffusion prior (prior_velocity) with a maximum displacement of 10 pixels.
+    The reference R = T moved by v is computed on the device by the forward map.
+    Returns (T [128][128] float32, v [1][2][64][64] float32)."""
+    wl = WORKLOADS["2d_warmstart_128"]
+    rng = np.random.default_rng([seed, index])
+    coords = centres(wl.image)
+    params = _blob_params(rng, int(rng.integers(4, 10)), 2, (0.04, 0.12), (0.4, 1.0), 0.15, 0.85)
+    T = gaussian_blobs(coords, params).astype(np.float32)
+    v = prior_velocity(wl.velocity, wl.alpha, WARMSTART_MAX_DISP_PX * min(wl.image.h),
+                       int(rng.integers(2 ** 31)))
+    return T, v
 
 
 def prior_velocity(g: GridSpec, alpha: float, max_disp: float, seed: int, eps: float = 1e-3):

@@ -1,0 +1,198 @@
+"""Learned warm start of the Gauss-Newton solve (an addition; the paper starts
+every solve of Eq. 11 from zero or from a coarser level).
+
+Pipeline, on one GPU, through the lgnk C ABI:
+  1. pairs: T = random Gaussian blobs, v_true from the diffusion prior with at
+     most 10 pixels of displacement (``synth.warmstart_pair``), R = u1(v_true, T)
+     by the forward map (lgnk_forward);
+  2. targets: v* = the zero-initialised Gauss-Newton solution of each training
+     pair (lgnk_solve), i.e. the network learns what the solver returns;
+  3. training: the lgnk_ws encoder-decoder (bf16 weights, FP32 accumulation,
+     Adam with a cosine learning-rate decay) on (T, R) -> v*;
+  4. evaluation on held-out pairs: Gauss-Newton from v = 0 with |g| <= 1e-3
+     |g(0)| against Gauss-Newton from the prediction to the same absolute
+     gradient norm.  The solver stays the judge: when the prediction does not
+     lower the objective below J(0), the solve starts from zero instead.
+
+``python -m paper_1703_04446_gb300.warmstart`` runs the whole pipeline and
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import lgnk, synth
+
+WORKLOAD = "2d_warmstart_128"
+SCALE = 0.05            # network output scale: velocities are O(10 px) = O(0.08)
+SOLVE = dict(max_gn=50, max_pcg=50, pcg_rtol=0.1)
+
+
+def problem():
+    return lgnk.Problem.from_workload(synth.WORKLOADS[WORKLOAD])
+
+
+def make_pairs(ctx: lgnk.Context, first: int, count: int, seed: int = 0):
+    """(T [n][128][128], R, v_true [n][1][2][64][64]) on the device."""
+    wl = synth.WORKLOADS[WORKLOAD]
+    m = wl.image.m[0]
+    mv = wl.velocity.m[0]
+    T = torch.empty((count, m, m), device=ctx.device)
+    R = torch.empty_like(T)
+    V = torch.empty((count, 1, 2, mv, mv), device=ctx.device)
+    for k in range(count):
+        t, v = synth.warmstart_pair(first + k, seed)
+        T[k].copy_(torch.from_numpy(t))
+        V[k].copy_(torch.from_numpy(v))
+        R[k].copy_(ctx.forward(V[k], T[k]))
+    return T, R, V
+
+
+def solve_targets(ctx: lgnk.Context, T, R, rtol: float = 1e-3):
+    """Zero-initialised Gauss-Newton solutions and their reports."""
+    V = torch.empty((T.shape[0],) + tuple(ctx.problem.velocity_shape), device=ctx.device)
+    reports = []
+    for k in range(T.shape[0]):
+        v, rep = ctx.solve(T[k], R[k], None, gn_grad_rtol=rtol, **SOLVE)
+        V[k].copy_(v)
+        reports.append(rep)
+    return V, reports
+
+
+def train(net: lgnk.WarmStart, T, R, V, epochs: int, batch: int, lr: float, seed: int = 0, lr_min: float = 1e-5):
+    """Adam on minibatches of shuffled pairs; cosine decay from lr to lr_min.
+    Returns the loss of every step."""
+    n = T.shape[0]
+    steps = epochs * (n // batch)
+    rng = np.random.default_rng(seed)
+    V2 = V.reshape(n, 2, V.shape[-2], V.shape[-1])
+    losses, step = [], 0
+    for _ in range(epochs):
+        order = torch.from_numpy(rng.permutation(n)).to(T.device)
+        for b in range(n // batch):
+            idx = order[b * batch:(b + 1) * batch]
+            rate = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * step / max(steps, 1)))
+            losses.append(net.train_step(T[idx].contiguous(), R[idx].contiguous(), V2[idx].contiguous(), rate))
+            step += 1
+    return losses
+
+
+def _sync():
+    torch.cuda.synchronize()
+
+
+def warm_solve(ctx: lgnk.Context, net: lgnk.WarmStart, T, R, gtol_abs: float):
+    """Gauss-Newton from the network's prediction to |g| <= gtol_abs; falls
+    back to v = 0 when the prediction does not lower J below J(0).
+    Returns (v, report, used_prediction)."""
+    v0 = net.predict(T[None], R[None]).reshape(ctx.problem.velocity_shape)
+    zero = torch.zeros_like(v0)
+    J0 = ctx.objective(zero, T, R)[0]
+    Jp = ctx.objective(v0, T, R)[0]
+    used = Jp < J0
+    start = v0 if used else zero
+    v, rep = ctx.solve(T, R, start, gn_grad_rtol=0.0, gn_grad_atol=gtol_abs, **SOLVE)
+    return v, rep, used
+
+
+def evaluate(ctx: lgnk.Context, net: lgnk.WarmStart, T, R, rtol: float = 1e-3):
+    """Per held-out pair: zero-initialised solve to |g| <= rtol |g(0)|, then the
+    warm-started solve to the same absolute gradient norm; wall times include
+    the prediction and the J(0), J(v0) checks."""
+    rows = []
+    for k in range(T.shape[0]):
+        _sync()
+        t0 = time.perf_counter()
+        vz, rz = ctx.solve(T[k], R[k], None, gn_grad_rtol=rtol, **SOLVE)
+        _sync()
+        t1 = time.perf_counter()
+        gtol = rtol * rz["g0"]
+        vw, rw, used = warm_solve(ctx, net, T[k], R[k], gtol)
+        _sync()
+        t2 = time.perf_counter()
+        rows.append(dict(zero_gn=rz["gn_iters"], zero_pcg=rz["pcg_iters"], zero_ms=1e3 * (t1 - t0),
+                         zero_J=rz["J"], zero_ok=rz["g"] <= gtol * (1 + 1e-12),
+                         warm_gn=rw["gn_iters"], warm_pcg=rw["pcg_iters"], warm_ms=1e3 * (t2 - t1),
+                         warm_J=rw["J"], warm_ok=rw["g"] <= gtol * (1 + 1e-12), used=bool(used),
+                         g0=rz["g0"], warm_g_start=rw["g0"]))
+    return rows
+
+
+def summarize(rows):
+    def stat(key):
+        a = np.array([r[key] for r in rows], dtype=np.float64)
+        return {"mean": float(a.mean()), "median": float(np.median(a))}
+    zt = sum(r["zero_ms"] for r in rows)
+    wt = sum(r["warm_ms"] for r in rows)
+    return {
+        "pairs": len(rows),
+        "zero": {"gn_iters": stat("zero_gn"), "pcg_iters": stat("zero_pcg"), "ms": stat("zero_ms"),
+                 "converged": int(sum(r["zero_ok"] for r in rows))},
+        "warm": {"gn_iters": stat("warm_gn"), "pcg_iters": stat("warm_pcg"), "ms": stat("warm_ms"),
+                 "converged": int(sum(r["warm_ok"] for r in rows)),
+                 "prediction_used": int(sum(r["used"] for r in rows))},
+        "time_ratio_zero_over_warm": zt / wt if wt > 0 else None,
+        "start_gradient_ratio": stat_ratio(rows),
+        "final_J_ratio_warm_over_zero": float(np.median([r["warm_J"] / r["zero_J"] for r in rows])),
+    }
+
+
+def stat_ratio(rows):
+    a = np.array([r["warm_g_start"] / r["g0"] for r in rows])
+    return {"median": float(np.median(a)), "max": float(a.max())}
+
+
+def run(n_train=2048, n_test=256, channels=32, epochs=30, batch=32, lr=1e-3, seed=0, log=None):
+    ctx = lgnk.Context(problem())
+    out = {"workload": WORKLOAD, "train_pairs": n_train, "test_pairs": n_test, "base_channels": channels,
+           "epochs": epochs, "batch": batch}
+    t = time.perf_counter()
+    T, R, _ = make_pairs(ctx, 0, n_train, seed)
+    Tt, Rt, _ = make_pairs(ctx, 1_000_000, n_test, seed)
+    _sync()
+    out["pairs_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    V, reps = solve_targets(ctx, T, R)
+    _sync()
+    out["targets_s"] = time.perf_counter() - t
+    out["targets_gn_iters_mean"] = float(np.mean([r["gn_iters"] for r in reps]))
+    net = lgnk.WarmStart(T.shape[-1], channels, batch, SCALE)
+    net.set_params(torch.from_numpy(synth.warmstart_init(channels, seed)))
+    t = time.perf_counter()
+    losses = train(net, T, R, V, epochs, batch, lr, seed)
+    _sync()
+    out["train_s"] = time.perf_counter() - t
+    out["train_steps"] = len(losses)
+    out["loss_first"], out["loss_last"] = losses[0], float(np.mean(losses[-20:]))
+    rows = evaluate(ctx, net, Tt, Rt)
+    out["eval"] = summarize(rows)
+    if log:
+        with open(log, "w") as f:
+            json.dump({"summary": out, "rows": rows, "losses": losses}, f)
+    net.close()
+    ctx.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--train", type=int, default=2048)
+    ap.add_argument("--test", type=int, default=256)
+    ap.add_argument("--channels", type=int, default=32)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--log", default=None, help="JSON file for per-pair rows and losses")
+    a = ap.parse_args()
+    print(json.dumps(run(a.train, a.test, a.channels, a.epochs, a.batch, a.lr, a.seed, a.log)))
+
+
+if __name__ == "__main__":
+    main()

@@ -100,3 +100,22 @@ def test_binding_fails_loudly_without_library(tmp_path):
             lgnk.load_library(str(tmp_path / "missing.so"))
     finally:
         lgnk._lib = saved
+
+
+@pytest.mark.parametrize("m,c,B,scale", [(12, 4, 1, 1.0), (4, 4, 1, 1.0), (16, 0, 1, 1.0), (16, 4, 0, 1.0),
+                                         (16, 4, 1, 0.0), (16, 4, 1, -1.0), (16, 300, 1, 1.0)])
+def test_warm_start_create_rejects_bad_shapes_before_any_device_call(lib, m, c, B, scale):
+    h = ctypes.c_void_p()
+    assert lib.lgnk_ws_create(m, c, B, ctypes.c_float(scale), None, ctypes.byref(h)) == 1
+    assert not h.value
+
+
+def test_warm_start_null_handle_is_rejected(lib):
+    assert lib.lgnk_ws_create(16, 4, 1, ctypes.c_float(1.0), None, None) == 1
+    assert lib.lgnk_ws_num_params(None) == 0
+    assert lib.lgnk_ws_predict(None, 1, None, None, None) == 1
+    assert lib.lgnk_ws_train_step(None, 1, None, None, None, ctypes.c_float(1e-3), None) == 1
+    for name in ("lgnk_ws_set_params", "lgnk_ws_get_params", "lgnk_ws_get_grads"):
+        assert getattr(lib, name)(None, None) == 1
+    assert lib.lgnk_ws_last_error(None)
+    lib.lgnk_ws_destroy(None)
