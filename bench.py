@@ -425,6 +425,12 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     objgrad_ms = og_ev[0].elapsed_time(og_ev[1]) / 10
     others = {} if args.no_other_workloads else other_workloads(dev)
+    warm = None
+    if args.warm_start:
+        # learned warm start: 2048 solver-generated 128^2 training pairs, 256
+        # held-out pairs (about three minutes, so only on request)
+        from paper_1703_04446_gb300 import warmstart
+        warm = warmstart.run()
     tts = None
     if not args.no_solve:
         torch.cuda.synchronize(dev)
@@ -476,7 +482,8 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "extra": {"forward_voxel_steps_per_s": voxel_steps / (fwd_ms * 1e-3), "forward_ms": fwd_ms,
-                  "objective_gradient_ms": objgrad_ms, "time_to_solution": tts, "other_workloads": others},
+                  "objective_gradient_ms": objgrad_ms, "time_to_solution": tts, "other_workloads": others,
+                  **({"warm_start": warm} if warm is not None else {})},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ins)
@@ -493,6 +500,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="also train and evaluate the learned warm start (2D 128^2 pairs, about 3 min)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

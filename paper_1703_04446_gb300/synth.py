@@ -96,7 +96,7 @@ WORKLOADS = {
     # image pairs of the learned warm start (128^2 images, stationary 64^2 velocity)
     "2d_warmstart_128": Workload(
         "2d_warmstart_128", _box((128, 128)), _box((64, 64)), 1, 4,
-        "transport", "diffusion", 1e-2, 0.0),
+        "transport", "diffusion", 1e-3, 0.0),
 }
 
 WARMSTART_MAX_DISP_PX = 10.0
