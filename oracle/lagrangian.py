@@ -22,6 +22,11 @@ Readings of the paper taken here (where it is silent or garbled):
   t = 0 (dt = +1/N); stage times t_k, t_k + dt/2, t_k + dt/2, t_k + dt.
 * The push-forward matrix with particle width equal to the cell size is the
   transpose of the linear interpolation matrix (Sec. 3.1, end of Step 2).
+* The general PIC kernel (Eqs. 7-8 with any width delta): each particle is the
+  tensor product of normalised 1D hats of half-width delta (unit mass), and
+  cell i receives the exact integral of the particle over the cell (Eq. 8), so
+  the columns of F sum to one for any delta and h.  ``delta=None`` selects the
+  width-equals-cell-size case above.
 """
 from __future__ import annotations
 
@@ -128,6 +133,91 @@ def scatter_gradient(values: np.ndarray, dp: np.ndarray, grid: Grid, p: np.ndarr
         contrib = values * np.sum(dw * dp, axis=0)
         np.add.at(out, flat[inside], contrib[inside])
     return out.reshape(grid.shape)
+
+
+def _hat_cdf(s):
+    """Integral of the unit-mass hat max(0, 1 - |x|) from -inf to s."""
+    s = np.clip(s, -1.0, 1.0)
+    return np.where(s <= 0.0, 0.5 * (1.0 + s) ** 2, 1.0 - 0.5 * (1.0 - s) ** 2)
+
+
+def _hat(s):
+    return np.maximum(0.0, 1.0 - np.abs(s))
+
+
+def _hat_cells(grid: Grid, p: np.ndarray, delta: float):
+    """For every cell that the hat particle of half-width delta at each point can
+    overlap: the flat index (-1 outside the grid), the mass fraction (Eq. 8,
+    exact integral of the particle over the cell) and its derivative with
+    respect to the particle position, per axis."""
+    d = grid.d
+    per_axis = []
+    for a in range(d):
+        lo = np.floor((p[a] - delta - grid.lo[a]) / grid.h[a]).astype(np.int64)
+        hi = np.floor((p[a] + delta - grid.lo[a]) / grid.h[a]).astype(np.int64)
+        n = int((hi - lo).max()) + 1 if p.shape[1] else 1
+        cells = []
+        for o in range(n):
+            i = lo + o
+            e0 = grid.lo[a] + i * grid.h[a]          # faces of cell i
+            e1 = e0 + grid.h[a]
+            w = _hat_cdf((e1 - p[a]) / delta) - _hat_cdf((e0 - p[a]) / delta)
+            dw = (_hat((e0 - p[a]) / delta) - _hat((e1 - p[a]) / delta)) / delta
+            cells.append((i, w, dw))
+        per_axis.append(cells)
+    strides = [int(np.prod(grid.m[:a])) for a in range(d)]
+    out = []
+    for combo in itertools.product(*per_axis):
+        inside = np.ones(p.shape[1], dtype=bool)
+        flat = np.zeros(p.shape[1], dtype=np.int64)
+        for a, (i, _, _) in enumerate(combo):
+            inside &= (i >= 0) & (i < grid.m[a])
+            flat += i * strides[a]
+        w = np.prod([c[1] for c in combo], axis=0)
+        dw = []
+        for a in range(d):
+            g = combo[a][2].copy()
+            for b in range(d):
+                if b != a:
+                    g = g * combo[b][1]
+            dw.append(g)
+        out.append((np.where(inside, flat, -1), w, np.stack(dw)))
+    return out
+
+
+def scatter_hat(values: np.ndarray, grid: Grid, p: np.ndarray, delta: float) -> np.ndarray:
+    """PIC push-forward with hat particles of half-width delta (Eqs. 7-8):
+    out_i = sum_j values_j F_ij, F_ij = integral over cell i of particle j."""
+    out = np.zeros(grid.size)
+    for flat, w, _ in _hat_cells(grid, p, delta):
+        inside = flat >= 0
+        np.add.at(out, flat[inside], (w * values)[inside])
+    return out.reshape(grid.shape)
+
+
+def scatter_hat_gradient(values: np.ndarray, dp: np.ndarray, grid: Grid, p: np.ndarray,
+                         delta: float) -> np.ndarray:
+    """Derivative of ``scatter_hat`` along the point displacement dp."""
+    out = np.zeros(grid.size)
+    for flat, _, dw in _hat_cells(grid, p, delta):
+        inside = flat >= 0
+        np.add.at(out, flat[inside], (values * np.sum(dw * dp, axis=0))[inside])
+    return out.reshape(grid.shape)
+
+
+def gather_hat(F: np.ndarray, grid: Grid, p: np.ndarray, delta: float, gradient: bool = False):
+    """Transpose of ``scatter_hat``: sum_i F_ij F_i per point, and optionally its
+    gradient with respect to the point (the continuity J^T seed)."""
+    f = F.reshape(-1)
+    val = np.zeros(p.shape[1])
+    grad = np.zeros(p.shape) if gradient else None
+    for flat, w, dw in _hat_cells(grid, p, delta):
+        inside = flat >= 0
+        fv = np.where(inside, f[np.where(inside, flat, 0)], 0.0)
+        val += w * fv
+        if gradient:
+            grad += dw * fv
+    return (val, grad) if gradient else val
 
 
 def _time_nodes(K: int, t: float):
@@ -267,19 +357,22 @@ def euler_characteristics(v, vgrid: Grid, x, N: int, direction: int):
 # Final states u1(v) and their derivatives (Sec. 3.1 Step 2, Sec. 3.2)
 # ---------------------------------------------------------------------------
 
-def final_state(model: str, v, vgrid: Grid, T, igrid: Grid, N: int):
+def final_state(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, delta=None):
     """u1(v): transport pull-back u1 = T(y(v, x_c, 1, 0)) (Eq. 6) or continuity
-    push-forward u1 = F(y(v, x_c, 0, 1)) T(x_c) (Eq. 7).  Returns (u1, y)."""
+    push-forward u1 = F(y(v, x_c, 0, 1)) T(x_c) (Eq. 7; delta: PIC half-width,
+    None for width = cell size).  Returns (u1, y)."""
     x = cell_centres(igrid)
     y, _, _ = characteristics(v, vgrid, x, N, _direction(model))
     if model == "transport":
         u1 = interpolate(T, igrid, y).reshape(igrid.shape)
-    else:
+    elif delta is None:
         u1 = scatter(np.asarray(T, dtype=np.float64).reshape(-1), igrid, y)
+    else:
+        u1 = scatter_hat(np.asarray(T, dtype=np.float64).reshape(-1), igrid, y, delta)
     return u1, y
 
 
-def jvp(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, dv):
+def jvp(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, dv, delta=None):
     """(d_v u1) dv.  Transport: grad T(y) . (d_v y) dv; continuity:
     d_y(F(y) T) (d_v y) dv (Sec. 3.2)."""
     x = cell_centres(igrid)
@@ -287,10 +380,13 @@ def jvp(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, dv):
     if model == "transport":
         _, gT = interpolate(T, igrid, y, gradient=True)
         return np.sum(gT * dy, axis=0).reshape(igrid.shape)
-    return scatter_gradient(np.asarray(T, dtype=np.float64).reshape(-1), dy, igrid, y)
+    Tf = np.asarray(T, dtype=np.float64).reshape(-1)
+    if delta is None:
+        return scatter_gradient(Tf, dy, igrid, y)
+    return scatter_hat_gradient(Tf, dy, igrid, y, delta)
 
 
-def jtvp(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, r):
+def jtvp(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, r, delta=None):
     """(d_v u1)^T r: the transpose of ``jvp``."""
     x = cell_centres(igrid)
     direction = _direction(model)
@@ -300,7 +396,10 @@ def jtvp(model: str, v, vgrid: Grid, T, igrid: Grid, N: int, r):
         _, gT = interpolate(T, igrid, y, gradient=True)
         lam = gT * r.reshape(-1)
     else:
-        _, gr = interpolate(r, igrid, y, gradient=True)
+        if delta is None:
+            _, gr = interpolate(r, igrid, y, gradient=True)
+        else:
+            _, gr = gather_hat(r, igrid, y, delta, gradient=True)
         lam = gr * np.asarray(T, dtype=np.float64).reshape(-1)
     return characteristics_adjoint(v, vgrid, hist, N, direction, lam)
 

@@ -41,6 +41,7 @@ class Problem:
     gamma: float = 0.0
     mu: float = 1.0
     lam: float = 0.0
+    delta: float = None             # PIC half-width (continuity); None: width = cell size
 
     @property
     def time_weight(self) -> float:
@@ -176,7 +177,7 @@ def ssd(u1: np.ndarray, R: np.ndarray, igrid: Grid) -> float:
 
 def objective(prob: Problem, v, T, R):
     """J(v) = D(u1(v), R) + alpha S(v) (Eq. 9).  Returns (J, D, S, u1)."""
-    u1, _ = final_state(prob.model, v, prob.vgrid, T, prob.igrid, prob.N)
+    u1, _ = final_state(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, prob.delta)
     D = ssd(u1, R, prob.igrid)
     S = reg_value(prob, v)
     return D + prob.alpha * S, D, S, u1
@@ -184,14 +185,14 @@ def objective(prob: Problem, v, T, R):
 
 def gradient(prob: Problem, v, T, R):
     """d_v J = (d_v u1)^T h^d res + alpha dt h^d B^T B v."""
-    u1, _ = final_state(prob.model, v, prob.vgrid, T, prob.igrid, prob.N)
+    u1, _ = final_state(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, prob.delta)
     res = u1 - np.asarray(R, dtype=np.float64)
-    g = jtvp(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, prob.igrid.cell_volume * res)
+    g = jtvp(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, prob.igrid.cell_volume * res, prob.delta)
     return g + prob.alpha * reg_operator(prob, v)
 
 
 def hessvec(prob: Problem, v, T, p):
     """H p = (d_v u1)^T h^d (d_v u1) p + alpha dt h^d B^T B p + gamma p."""
-    du = jvp(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, p)
-    Hp = jtvp(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, prob.igrid.cell_volume * du)
+    du = jvp(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, p, prob.delta)
+    Hp = jtvp(prob.model, v, prob.vgrid, T, prob.igrid, prob.N, prob.igrid.cell_volume * du, prob.delta)
     return Hp + prob.alpha * reg_operator(prob, p) + prob.gamma * np.asarray(p, dtype=np.float64)
