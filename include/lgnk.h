@@ -78,6 +78,12 @@ typedef struct {
     double gamma;
     double mu_lame;     /* elastic only */
     double lambda_lame; /* elastic only */
+    /* continuity only: PIC particle half-width delta in domain units (Eqs. 7-8).
+     * 0: width equal to the cell size, F = P(y)^T (the experiments' choice).
+     * delta > 0: each particle is the tensor product of unit-mass hats of
+     * half-width delta, integrated exactly over every cell (mass-preserving
+     * for any delta); delta / h <= 3.5 on every axis.  Transport requires 0. */
+    double pic_delta;
 } lgnk_problem;
 
 typedef struct lgnk_ctx lgnk_ctx;

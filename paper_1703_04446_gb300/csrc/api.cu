@@ -125,6 +125,13 @@ const char* validate_problem(const lgnk_problem* p) {
     if (p->regularizer == LGNK_ELASTIC &&
         (!(p->mu_lame >= 0.0) || !(p->lambda_lame + p->mu_lame >= 0.0) || !std::isfinite(p->lambda_lame)))
         return "elastic needs mu >= 0 and lambda + mu >= 0";
+    if (!(p->pic_delta >= 0.0) || !std::isfinite(p->pic_delta)) return "pic_delta must be finite and >= 0";
+    if (p->pic_delta > 0.0) {
+        if (p->model != LGNK_CONTINUITY) return "pic_delta applies to the continuity model only";
+        for (int a = 0; a < d; ++a)
+            if (p->pic_delta * p->image.m[a] / (p->image.hi[a] - p->image.lo[a]) > 3.5 * (1.0 + 1e-9))
+                return "pic_delta must be at most 3.5 image cells on every axis";
+    }
     double ipad = 1.0, vpad = 1.0, M = 1.0;
     for (int a = 0; a < d; ++a) {
         ipad *= p->image.m[a] + 2 * LGNK_PAD;
@@ -190,6 +197,10 @@ TraceArgs base_args(const lgnk_ctx* ctx) {
             a.vxi_bf[i] = 0.0f;
         }
     }
+    for (int i = 0; i < 3; ++i)
+        a.pic_rho[i] = i < ctx->d ? (float)(ctx->prob.pic_delta * ctx->prob.image.m[i] /
+                                            (ctx->prob.image.hi[i] - ctx->prob.image.lo[i]))
+                                  : 0.0f;
     a.slice_nodes = (long long)ctx->vpad;
     a.V = ctx->Vp;
     a.dV = ctx->dVp;

@@ -53,6 +53,7 @@ struct TraceArgs {
     // vxi_a[a] + (i + 1/2) * vxi_b[a]  (exact in FP64: (x_c - lo_v) / h_v - 1/2)
     double vxi_a[3], vxi_b[3];
     float vxi_af[3], vxi_bf[3];  // the same in FP32 (per-stage recomputation)
+    float pic_rho[3];         // continuity PIC half-width in image cells per axis (0: width = cell)
     long long slice_nodes;    // padded velocity nodes per time slice
     const void* V;            // pair-packed velocity slices [m][zp][yp][xp] x [v(node) | v(node+1)]
     const void* dV;           // pair-packed direction slices (JVP, HESS)

@@ -412,6 +412,88 @@ __device__ __forceinline__ void splat_image(const DevGrid& g, const Start<D>& s,
     }
 }
 
+// General-width PIC push-forward (Eqs. 7-8): the particle is the tensor
+// product of unit-mass hats max(0, 1 - |s| / rho) / rho of half-width rho
+// cells; cell c (node coordinates [c - 1/2, c + 1/2]) receives the exact
+// integral of the particle over it, a difference of the hat's antiderivative,
+// so the weights of a particle sum to one.  Cells outside the grid are
+// dropped.  rho <= 3.5 keeps a particle within kHatMax cells per axis.
+constexpr int kHatMax = 8;
+
+__device__ __forceinline__ float hat_cdf(float s) {
+    s = fminf(fmaxf(s, -1.0f), 1.0f);
+    return s <= 0.0f ? 0.5f * (1.0f + s) * (1.0f + s) : 1.0f - 0.5f * (1.0f - s) * (1.0f - s);
+}
+
+__device__ __forceinline__ float hat_pdf(float s) { return fmaxf(0.0f, 1.0f - fabsf(s)); }
+
+// Cells [I0 + c0, I0 + c0 + n) of one axis that a particle at node coordinate
+// I0 + t overlaps inside the grid, their weights and d(weight)/dy.
+__device__ __forceinline__ void hat_axis(float t, float rho, int I0, int m, float inv_h, int& c0, int& n, float* w,
+                                         float* dw) {
+    t = fminf(fmaxf(t, -(float)I0 - rho - 2.0f), (float)(m - I0) + rho + 2.0f);   // also maps NaN into range
+    const int lo = max((int)floorf(t - rho + 0.5f), -I0);
+    const int hi = min((int)floorf(t + rho + 0.5f), m - 1 - I0);
+    c0 = lo;
+    n = min(hi - lo + 1, kHatMax);
+    const float ir = 1.0f / rho;
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+        const float c = (float)(lo + j);
+        const float s1 = (c + 0.5f - t) * ir, s0 = (c - 0.5f - t) * ir;
+        w[j] = hat_cdf(s1) - hat_cdf(s0);
+        dw[j] = (hat_pdf(s0) - hat_pdf(s1)) * ir * inv_h;
+    }
+}
+
+// KIND 0: acc += mass w (push-forward); KIND 1: acc += mass (grad_y w . dp)
+// (its tangent); KIND 2: grad = sum_c grad_y w_c F_c (the transpose's seed).
+// acc and F are padded image grids.
+template <int D, int KIND>
+__device__ __noinline__ void pic_hat(const DevGrid& g, const int* I0, const float* u, const float* rho, float* acc,
+                                     const float* __restrict__ F, float mass, const float* dp, float* grad) {
+    int c0[3] = {0, 0, 0}, n[3] = {1, 1, 1};
+    float w[3][kHatMax], dw[3][kHatMax];
+    w[2][0] = 1.0f;
+    dw[2][0] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) hat_axis(u[a] * g.inv_h[a], rho[a], I0[a], g.m[a], g.inv_h[a], c0[a], n[a], w[a], dw[a]);
+    float gsum[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+    for (int kz = 0; kz < n[2]; ++kz) {
+#pragma unroll 1
+        for (int ky = 0; ky < n[1]; ++ky) {
+            const float wyz = w[1][ky] * w[2][kz];
+            const float dyz = dw[1][ky] * w[2][kz], ydz = w[1][ky] * dw[2][kz];
+            int p[3];
+            p[1] = I0[1] + c0[1] + ky + LGNK_PAD;
+            p[2] = D == 3 ? I0[2] + c0[2] + kz + LGNK_PAD : 0;
+#pragma unroll 1
+            for (int kx = 0; kx < n[0]; ++kx) {
+                p[0] = I0[0] + c0[0] + kx + LGNK_PAD;
+                const int o = linear<D>(g, p);
+                const float gx = dw[0][kx] * wyz, gy = w[0][kx] * dyz, gz = w[0][kx] * ydz;
+                if (KIND == 0) {
+                    atomicAdd(acc + o, mass * w[0][kx] * wyz);
+                } else if (KIND == 1) {
+                    float x = fmaf(gx, dp[0], gy * dp[1]);
+                    if (D == 3) x = fmaf(gz, dp[2], x);
+                    atomicAdd(acc + o, mass * x);
+                } else {
+                    const float f = __ldg(F + o);
+                    gsum[0] = fmaf(gx, f, gsum[0]);
+                    gsum[1] = fmaf(gy, f, gsum[1]);
+                    gsum[2] = fmaf(gz, f, gsum[2]);
+                }
+            }
+        }
+    }
+    if (KIND == 2) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) grad[a] = gsum[a];
+    }
+}
+
 // Slices of the stages of step k: t_k (2k), t_k + dt/2 (2k + 1, stages 2 and
 // 3), t_k + dt (2k + 2); a stationary field has the single slice 0.
 template <bool NS>
@@ -689,7 +771,18 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_ke
             }
         } else {
             const float mass = __ldg(A.T + vox);
-            if (MODE == MODE_FWD) {
+            if (A.pic_rho[0] > 0.0f) {
+                if (MODE == MODE_FWD) {
+                    pic_hat<D, 0>(A.ig, si.I0, u, A.pic_rho, A.acc, nullptr, mass, nullptr, nullptr);
+                } else if (MODE == MODE_JVP) {
+                    pic_hat<D, 1>(A.ig, si.I0, u, A.pic_rho, A.acc, nullptr, mass, dy, nullptr);
+                } else if (MODE == MODE_JTVP) {
+                    float gr[D];
+                    pic_hat<D, 2>(A.ig, si.I0, u, A.pic_rho, nullptr, A.r, 0.0f, nullptr, gr);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) lam[a] = mass * gr[a];
+                }
+            } else if (MODE == MODE_FWD) {
                 splat_image<D, false>(A.ig, si, A.acc, u, mass, nullptr);
             } else if (MODE == MODE_JVP) {
                 splat_image<D, true>(A.ig, si, A.acc, u, mass, dy);

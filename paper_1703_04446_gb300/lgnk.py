@@ -45,7 +45,7 @@ class _Problem(ctypes.Structure):
     _fields_ = [("image", _Grid), ("velocity", _Grid), ("time_nodes", ctypes.c_int),
                 ("rk4_steps", ctypes.c_int), ("model", ctypes.c_int), ("distance", ctypes.c_int),
                 ("regularizer", ctypes.c_int), ("alpha", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("mu_lame", ctypes.c_double), ("lambda_lame", ctypes.c_double)]
+                ("mu_lame", ctypes.c_double), ("lambda_lame", ctypes.c_double), ("pic_delta", ctypes.c_double)]
 
 
 class _SolveOpts(ctypes.Structure):
@@ -143,6 +143,7 @@ class Problem:
     velocity_hi: tuple = None
     mu_lame: float = 1.0
     lambda_lame: float = 0.0
+    pic_delta: float = 0.0      # continuity PIC half-width (domain units); 0: width = cell size
     extra: dict = field(default_factory=dict)
 
     def __post_init__(self):
@@ -195,6 +196,7 @@ class Problem:
         p.gamma = float(self.gamma)
         p.mu_lame = float(self.mu_lame)
         p.lambda_lame = float(self.lambda_lame)
+        p.pic_delta = float(self.pic_delta)
         return p
 
 

@@ -14,7 +14,13 @@ CASES = {
     "3d_transport_ragged": ((20, 18, 17), (10, 9, 9), (0, 0, 0), (1, 1, 1), 1, 8, "transport", "diffusion", 2.5),
     "3d_transport_K2_N1": ((12, 12, 12), (6, 6, 6), (0, 0, 0), (1, 1, 1), 2, 1, "transport", "diffusion", 2.0),
     "3d_continuity_K2": ((16, 20, 12), (8, 10, 6), (0, 0, 0), (1.0, 1.25, 0.75), 2, 3, "continuity", "diffusion", 2.0),
+    "2d_continuity_hat_K3": ((40, 36), (20, 18), (0, 0), (1.0, 0.9), 3, 6, "continuity", "diffusion", 2.5),
+    "2d_continuity_hat_widest": ((32, 32), (16, 16), (0, 0), (1, 1), 1, 4, "continuity", "diffusion", 2.0),
+    "3d_continuity_hat_K2": ((18, 16, 14), (9, 8, 7), (0, 0, 0), (1.0, 0.9, 0.8), 2, 3, "continuity", "diffusion", 2.0),
 }
+
+# general-width PIC cases: particle half-width delta in units of the smallest image cell
+PIC_DELTA = {"2d_continuity_hat_K3": 1.7, "2d_continuity_hat_widest": 3.5, "3d_continuity_hat_K2": 0.6}
 
 
 def make_case(name, seed=0, alpha=1e-2, gamma=1e-3):
@@ -39,11 +45,12 @@ def make_case(name, seed=0, alpha=1e-2, gamma=1e-3):
     r = rng.normal(size=T.shape)
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     arrays = {k: f32(a) for k, a in dict(T=T, R=R, v=v, dv=dv, r=r).items()}
+    delta = PIC_DELTA[name] * h if name in PIC_DELTA else None
     oprob = OProblem(L.Grid(im, lo, hi), L.Grid(vm, lo, hi), K=K, N=N, model=model, reg=reg, alpha=alpha,
-                     gamma=gamma, mu=1.0, lam=0.5)
+                     gamma=gamma, mu=1.0, lam=0.5, delta=delta)
     gprob = dict(image_m=im, velocity_m=vm, time_nodes=K, rk4_steps=N, model=model, regularizer=reg, alpha=alpha,
                  gamma=gamma, image_lo=lo, image_hi=hi, velocity_lo=lo, velocity_hi=hi, mu_lame=1.0,
-                 lambda_lame=0.5)
+                 lambda_lame=0.5, pic_delta=delta or 0.0)
     return oprob, gprob, arrays
 
 

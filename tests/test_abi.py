@@ -58,7 +58,8 @@ def _problem(**over):
 @pytest.mark.parametrize("field,value,msg", [
     ("rk4_steps", 0, b"rk4_steps"), ("rk4_steps", 65, b"rk4_steps"), ("time_nodes", 0, b"time_nodes"),
     ("model", 5, b"model"), ("regularizer", 9, b"regularizer"), ("alpha", -1.0, b"alpha"),
-    ("gamma", float("nan"), b"gamma"),
+    ("gamma", float("nan"), b"gamma"), ("pic_delta", -0.1, b"pic_delta"), ("pic_delta", float("inf"), b"pic_delta"),
+    ("pic_delta", 0.01, b"continuity model only"),
 ])
 def test_create_rejects_invalid_problem_before_any_device_call(lib, field, value, msg):
     pc = _problem()
@@ -67,6 +68,13 @@ def test_create_rejects_invalid_problem_before_any_device_call(lib, field, value
     st = lib.lgnk_create(ctypes.byref(pc), None, 0, ctypes.byref(h))
     assert st == 1 and not h.value
     assert msg in lib.lgnk_last_error(None)
+
+
+def test_create_rejects_too_wide_pic_particles(lib):
+    pc = _problem(model="continuity", pic_delta=3.6 / 16)
+    h = ctypes.c_void_p()
+    assert lib.lgnk_create(ctypes.byref(pc), None, 0, ctypes.byref(h)) == 1
+    assert b"3.5 image cells" in lib.lgnk_last_error(None)
 
 
 def test_create_rejects_bad_grids(lib):

@@ -23,10 +23,10 @@ TOL = 1e-5
 def _oracle(name):
     op, gp, a = make_case(name)
     f64 = {k: v.astype(np.float64) for k, v in a.items()}
-    u1, y = L.final_state(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N)
+    u1, y = L.final_state(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N, op.delta)
     out = dict(u1=u1, y=y,
-               jvp=L.jvp(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N, f64["dv"]),
-               jtvp=L.jtvp(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N, f64["r"]),
+               jvp=L.jvp(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N, f64["dv"], op.delta),
+               jtvp=L.jtvp(op.model, f64["v"], op.vgrid, f64["T"], op.igrid, op.N, f64["r"], op.delta),
                hess=hessvec(op, f64["v"], f64["T"], f64["dv"]),
                obj=objective(op, f64["v"], f64["T"], f64["R"])[:3],
                grad=gradient(op, f64["v"], f64["T"], f64["R"]),
