@@ -220,6 +220,45 @@ def profiled_traffic():
         return None
 
 
+def assembled_matvec(ctx, v, T, dv, stream, reps=50):
+    """The assembled-J variant on the benchmark workload (outside the timed
+    region): assembly time, blocks per voxel, the Hessian matvec through the
+    stored rows (whole call and its ELL kernel), and the bytes one ELL HESS
+    launch must read at least (counts, keys and blocks of every row, once)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(2):
+        blocks = ctx.assemble(v, T)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(5):
+        ctx.assemble(v, T)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    asm_ms = ev[0].elapsed_time(ev[1]) / 5
+    out = torch.empty_like(dv)
+    for _ in range(5):
+        ctx.hessvec_assembled(dv, out=out)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        ctx.hessvec_assembled(dv, out=out)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    hv_ms = ev[0].elapsed_time(ev[1]) / reps
+    ctx.profile(True)
+    for _ in range(reps):
+        ctx.hessvec_assembled(dv, out=out)
+    ell_ms, n_ell, _ = ctx.profile_read()
+    ctx.profile(False)
+    M = T.numel()
+    d = T.dim()
+    row_bytes = 4 * M + blocks * (8 + 4 * (2 ** d) * d)
+    return {"assemble_ms": asm_ms, "blocks_per_voxel": blocks / M, "hessvec_ms": hv_ms,
+            "matvecs_per_s": 1e3 / hv_ms, "ell_kernel_ms": ell_ms / max(n_ell, 1),
+            "ell_min_bytes": row_bytes, "ell_min_bytes_gbs": row_bytes / (ell_ms / max(n_ell, 1) * 1e-3) / 1e9}
+
+
 def other_workloads(dev, names=("2d_continuity_256", "3d_continuity_brain")):
     """Matvec and forward times of the mass-preserving workloads (the continuity
     push-forward and its derivatives), measured outside the timed region."""
@@ -424,6 +463,7 @@ def run_gpu(args):
     og_ev[1].record(stream)
     torch.cuda.synchronize(dev)
     objgrad_ms = og_ev[0].elapsed_time(og_ev[1]) / 10
+    asm = assembled_matvec(ctx, tv, tT, tdv, stream)
     others = {} if args.no_other_workloads else other_workloads(dev)
     warm = None
     if args.warm_start:
@@ -439,7 +479,16 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         tts = {"seconds": time.perf_counter() - t0, "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters"],
                "hessvecs": rep["hessvecs"], "grad_ratio": rep["g"] / rep["g0"], "J0": rep["J0"], "J": rep["J"],
-               "status": rep["status_name"], "max_gn": args.max_gn}
+               "status": rep["status_name"], "max_gn": args.max_gn, "matvec": "assembled",
+               "assembled_gn": rep["assembled_gn"]}
+        # the same solve with the matrix-free products in every PCG iteration
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, rep = ctx.solve(tT, tR, None, max_gn=args.max_gn, gn_grad_rtol=1e-3, max_pcg=50, pcg_rtol=0.1, matvec=0)
+        torch.cuda.synchronize(dev)
+        tts["matrix_free"] = {"seconds": time.perf_counter() - t0, "gn_iters": rep["gn_iters"],
+                              "pcg_iters": rep["pcg_iters"], "grad_ratio": rep["g"] / rep["g0"], "J": rep["J"],
+                              "status": rep["status_name"]}
         # the paper's setting: multilevel continuation (3 levels, 32^3 / 64^3 / 128^3 images)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -482,12 +531,51 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "extra": {"forward_voxel_steps_per_s": voxel_steps / (fwd_ms * 1e-3), "forward_ms": fwd_ms,
-                  "objective_gradient_ms": objgrad_ms, "time_to_solution": tts, "other_workloads": others,
+                  "objective_gradient_ms": objgrad_ms, "time_to_solution": tts, "assembled": asm, "other_workloads": others,
                   **({"warm_start": warm} if warm is not None else {})},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ins)
     print(json.dumps(line), flush=True)
+
+
+def profile_case(args):
+    """A short fixed invocation of one kernel for ncu captures: an S^3
+    transport image (the benchmark's ellipsoid phantom), an (S/2)^3
+    stationary velocity, N = 8, alpha = 1e-2.  'hess' launches the fused
+    matrix-free matvec `launches` times; 'ell' assembles J once and then
+    launches the assembled matvec `launches` times; 'solve' runs `launches`
+    Gauss-Newton iterations (every kernel of the solver)."""
+    import torch
+    from paper_1703_04446_gb300 import lgnk, synth
+    S = args.size
+    lo, hi = (0.0,) * 3, (1.0,) * 3
+    ig = synth.GridSpec((S,) * 3, lo, hi)
+    vg = synth.GridSpec((S // 2,) * 3, lo, hi)
+    T = synth.ellipsoid_phantom(synth.centres(ig), np.random.default_rng(0), lo, hi).astype(np.float32)
+    h = 1.0 / S
+    v = synth.random_velocity(vg, 1, 8 * h, 7).astype(np.float32)
+    dv = synth.random_velocity(vg, 1, 2 * h, 5).astype(np.float32)
+    prob = lgnk.Problem(image_m=(S,) * 3, velocity_m=(S // 2,) * 3, time_nodes=1, rk4_steps=8, alpha=1e-2)
+    ctx = lgnk.Context(prob)
+    tv, tT, tdv = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (v, T, dv))
+    out = torch.empty_like(tdv)
+    if args.profile_case == "ell":
+        ctx.assemble(tv, tT)
+        for _ in range(args.launches):
+            ctx.hessvec_assembled(tdv, out=out)
+    elif args.profile_case == "solve":
+        # `launches` Gauss-Newton iterations from v = 0 towards the phantom moved by v
+        R = ctx.forward(tv, tT)
+        _, rep = ctx.solve(tT, R, None, max_gn=args.launches, gn_grad_rtol=1e-3, max_pcg=50, pcg_rtol=0.1)
+        out.copy_(tdv)
+        print(json.dumps({k: rep[k] for k in ("gn_iters", "pcg_iters", "hessvecs", "seconds")}))
+    else:
+        for _ in range(args.launches):
+            ctx.hessvec(tv, tT, tdv, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "size": S, "launches": args.launches,
+                      "checksum": float(out.double().abs().sum())}))
 
 
 def main():
@@ -500,9 +588,16 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true")
+    ap.add_argument("--profile-case", choices=["hess", "ell", "solve"], default=None,
+                    help="run only a short fixed invocation of one kernel (for ncu captures)")
+    ap.add_argument("--size", type=int, default=128, help="image cells per axis of --profile-case")
+    ap.add_argument("--launches", type=int, default=3, help="kernel launches of --profile-case")
     ap.add_argument("--warm-start", action="store_true",
                     help="also train and evaluate the learned warm start (2D 128^2 pairs, about 3 min)")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

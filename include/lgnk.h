@@ -46,7 +46,8 @@ typedef enum {
     LGNK_ERR_NUMERIC = 4,      /* NaN or Inf met in a reduction                */
     LGNK_ERR_INTERNAL = 5,
     LGNK_LS_FAILED = 6,        /* Armijo found no decrease; v keeps last iterate */
-    LGNK_NOT_CONVERGED = 7     /* informational: iteration cap reached          */
+    LGNK_NOT_CONVERGED = 7,    /* informational: iteration cap reached          */
+    LGNK_ERR_CAPACITY = 8      /* a fixed-capacity structure is too small       */
 } lgnk_status;
 
 typedef enum { LGNK_TRANSPORT = 0, LGNK_CONTINUITY = 1 } lgnk_model;   /* Eq. 2 / Eq. 3 */
@@ -128,6 +129,29 @@ lgnk_status lgnk_objective(lgnk_ctx* ctx, const float* v, const float* T, const 
  * Hdv[n] out. */
 lgnk_status lgnk_hessvec(lgnk_ctx* ctx, const float* v, const float* T, const float* dv, float* Hdv);
 
+/* Assembled J (transport).  The paper forms d_v u1 as a sparse matrix once per
+ * Gauss-Newton iteration and applies it in every PCG matvec (Sec. 3.3).  Here
+ * row i of J = d_v u1 is grad T(y_i)^T d_v y_i, computed by the adjoint sweep
+ * of characteristic i and stored as at most 16 (3D) / 32 (2D) blocks, one per
+ * (time slice, velocity cell) the characteristic's RK4 stages meet, each
+ * holding the 2^d corner vectors; the products then read these rows instead
+ * of re-tracing.
+ * lgnk_assemble(ctx, v, T, blocks): builds J at (v, T) (device v[n], T[M]);
+ * blocks: NULL or a host size_t receiving the number of blocks stored; the rows
+ * live in the context (allocated on first use within its memory budget:
+ * 16 x (8 + 96) bytes per voxel in 3D, 32 x (8 + 32) in 2D) until the next
+ * lgnk_assemble or lgnk_solve with matvec = 1, which replaces them.  Returns
+ * LGNK_ERR_CAPACITY when a characteristic meets more blocks than a row holds
+ * (large displacements, many time slices) and LGNK_ERR_INVALID_ARG for the
+ * continuity model.  Synchronises the stream.
+ * lgnk_jvp_assembled: du[M] = J dv[n]; lgnk_jtvp_assembled: gv[n] = J^T r[M];
+ * lgnk_hessvec_assembled: Hdv[n] as lgnk_hessvec at the assembled (v, T).
+ * They return LGNK_ERR_INVALID_ARG when the context holds no valid J. */
+lgnk_status lgnk_assemble(lgnk_ctx* ctx, const float* v, const float* T, size_t* blocks);
+lgnk_status lgnk_jvp_assembled(lgnk_ctx* ctx, const float* dv, float* du);
+lgnk_status lgnk_jtvp_assembled(lgnk_ctx* ctx, const float* r, float* gv);
+lgnk_status lgnk_hessvec_assembled(lgnk_ctx* ctx, const float* dv, float* Hdv);
+
 /* Spectral preconditioner (Sec. 3.2): z = P^-1 r with P = alpha dt h_v^d A + gamma I
  * applied through the DCT-II eigenbasis of the Neumann operator A; a zero
  * eigenvalue (gamma = 0, constant mode) takes the smallest nonzero one, keeping
@@ -168,6 +192,9 @@ typedef struct {
     int precond;          /* 1 = spectral preconditioner, 0 = none                 */
     int verbosity;        /* 0 silent, 1 one line per GN iteration on stderr       */
     double gn_grad_atol;  /* also stop when |g| <= atol (default 0: off)           */
+    int matvec;           /* 1 (default): assembled J per GN step (transport; the    */
+                          /* matrix-free products when it does not fit); 0: always   */
+                          /* matrix-free                                             */
 } lgnk_solve_opts;
 
 typedef struct {
@@ -179,6 +206,7 @@ typedef struct {
     double g0, g;
     double seconds;
     int status;           /* lgnk_status of the solve */
+    int assembled_gn;     /* GN iterations whose PCG used the assembled J */
 } lgnk_solve_report;
 
 /* Fill opts with the defaults listed above. */

@@ -14,9 +14,16 @@
 cudaError_t launch_trace_2d(bool nonstat, int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s);
 cudaError_t launch_trace_3d(bool nonstat, int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s);
 
+cudaError_t launch_ell_2d(int mode, const EllArgs& a, cudaStream_t s);
+cudaError_t launch_ell_3d(int mode, const EllArgs& a, cudaStream_t s);
+
 cudaError_t launch_trace(int d, bool nonstat, int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s) {
     return d == 3 ? launch_trace_3d(nonstat, model, mode, a, nblocks, s)
                   : launch_trace_2d(nonstat, model, mode, a, nblocks, s);
+}
+
+cudaError_t launch_ell(int d, int mode, const EllArgs& a, cudaStream_t s) {
+    return d == 3 ? launch_ell_3d(mode, a, s) : launch_ell_2d(mode, a, s);
 }
 
 struct lgnk_ctx {
@@ -38,12 +45,21 @@ struct lgnk_ctx {
     float *Tp = nullptr, *acc = nullptr, *rp = nullptr, *itmp = nullptr, *rtmp = nullptr;
     float *pc0 = nullptr, *pc1 = nullptr, *Cm[3] = {nullptr, nullptr, nullptr}, *inv_eig = nullptr;
     double* partial = nullptr;
+    double* cpartial = nullptr;   // per-block entry counts of the assembled rows
     int npartial = 0;
     double* dres = nullptr;
     double* hres = nullptr;       // pinned host mirror of dres
+    float* fsc = nullptr;         // PCG step lengths on the device (alpha, -alpha, beta)
     float* sv[7] = {nullptr};
     bool have_solve = false;
     float* ybuf = nullptr;        // end points [d][M] for lgnk_jacobian_determinant
+    // assembled J (transport, lgnk_assemble): ELL rows of asm_capacity(d) entries
+    long long* ekey = nullptr;
+    float* eblk = nullptr;
+    int* ecnt = nullptr;
+    int* eflag = nullptr;
+    bool asm_valid = false;
+    size_t asm_entries = 0;       // blocks in the assembled rows
     std::vector<void*> allocs;
     // profiling: CUDA events around every tracing-kernel launch, kernel counter
     bool prof = false;
@@ -400,6 +416,107 @@ lgnk_status hessvec_packed(lgnk_ctx* ctx, const float* T, const float* dv, float
     return reg_apply(ctx, dv, out, ctx->prob.alpha * ctx->wreg, ctx->prob.gamma, out);
 }
 
+EllArgs ell_args(const lgnk_ctx* ctx) {
+    EllArgs e{};
+    e.vg = ctx->vg;
+    e.M = (long long)ctx->M;
+    e.ekey = ctx->ekey;
+    e.eblk = ctx->eblk;
+    e.ecnt = ctx->ecnt;
+    e.dV = ctx->dVp;
+    e.G = ctx->Gp;
+    e.cellvol = (float)ctx->cellvol;
+    return e;
+}
+
+lgnk_status ell(lgnk_ctx* ctx, int mode, const EllArgs& e) {
+    if (ctx->prof) TRY(record_event(ctx));
+    KL(launch_ell(ctx->d, mode, e, ctx->stream));
+    ctx->trace_launches++;
+    if (ctx->prof) TRY(record_event(ctx));
+    return LGNK_OK;
+}
+
+// Rows of J = d_v u1 at the packed velocity and template (transport).  With
+// R: the same trace also yields u1 and the SSD (Eq. 10), and then
+// grad = J^T h^d (u1 - R) + alpha dt h_v^d A v is applied through the stored
+// rows (one ELL launch instead of a second trace), with J, D, S as in
+// objective_packed.  Returns LGNK_ERR_CAPACITY when a row overflows (grad and
+// the rows are then not valid).
+lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float* R = nullptr, float* grad = nullptr,
+                            double* J = nullptr, double* D = nullptr, double* S = nullptr) {
+    ctx->asm_valid = false;
+    const int W = asm_capacity(ctx->d);
+    const size_t B = ((size_t)1 << ctx->d) * ctx->d;
+    if (ctx->eflag == nullptr) {
+        TRY(dalloc(ctx, (size_t)W * ctx->M, &ctx->ekey));
+        TRY(dalloc(ctx, (size_t)W * B * ctx->M, &ctx->eblk));
+        TRY(dalloc(ctx, ctx->M, &ctx->ecnt));
+        TRY(dalloc(ctx, 1, &ctx->eflag));
+    }
+    CK(cudaMemsetAsync(ctx->eflag, 0, sizeof(int), ctx->stream));
+    TraceArgs a = base_args(ctx);
+    a.ekey = ctx->ekey;
+    a.eblk = ctx->eblk;
+    a.ecnt = ctx->ecnt;
+    a.eflag = ctx->eflag;
+    a.ewidth = W;
+    a.cpartial = ctx->cpartial;
+    if (R != nullptr) {
+        a.R = R;
+        a.u1 = ctx->itmp;
+        a.partial = ctx->partial;
+    }
+    TRY(trace(ctx, MODE_ASM, a));
+    KL(launch_reduce(ctx->cpartial, ctx->trace_blocks, ctx->dres + 7, ctx->stream));
+    int nfetch = 0;
+    if (R != nullptr) {
+        KL(launch_reduce(ctx->partial, ctx->trace_blocks, ctx->dres + 0, ctx->stream));
+        // grad = J^T (h^d res) through the rows, then the regularizer
+        TRY(zero_G(ctx));
+        EllArgs e = ell_args(ctx);
+        e.r = ctx->itmp;
+        TRY(ell(ctx, ELL_JTVP, e));
+        KL(launch_distribute_gradient(ctx->d, ctx->Gp, grad, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
+        TRY(reg_apply(ctx, v, grad, ctx->prob.alpha * ctx->wreg, 0.0, grad));
+        TRY(reg_apply(ctx, v, ctx->pc0, 1.0, 0.0, nullptr));
+        TRY(dot_dev(ctx, v, ctx->pc0, ctx->n, 1));
+        nfetch = 2;
+    }
+    CK(cudaMemcpyAsync(ctx->hres + 7, ctx->dres + 7, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hres + 6, ctx->eflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (nfetch) CK(cudaMemcpyAsync(ctx->hres, ctx->dres, nfetch * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int flag = 0;
+    memcpy(&flag, ctx->hres + 6, sizeof(int));
+    ctx->asm_entries = (size_t)ctx->hres[7];
+    if (flag != 0) {
+        SETERR("a characteristic meets more than %d (time slice, velocity cell) pairs: J not assembled", W);
+        return LGNK_ERR_CAPACITY;
+    }
+    ctx->asm_valid = true;
+    if (R != nullptr) {
+        const double Dv = 0.5 * ctx->cellvol * ctx->hres[0];
+        const double Sv = 0.5 * ctx->wreg * ctx->hres[1];
+        if (!std::isfinite(Dv) || !std::isfinite(Sv)) {
+            SETERR("non-finite objective");
+            return LGNK_ERR_NUMERIC;
+        }
+        if (D) *D = Dv;
+        if (S) *S = Sv;
+        if (J) *J = Dv + ctx->prob.alpha * Sv;
+    }
+    return LGNK_OK;
+}
+
+lgnk_status hessvec_assembled_packed(lgnk_ctx* ctx, const float* dv, float* out) {
+    TRY(pack_v(ctx, dv, ctx->dVp));
+    TRY(zero_G(ctx));
+    TRY(ell(ctx, ELL_HESS, ell_args(ctx)));
+    KL(launch_distribute_gradient(ctx->d, ctx->Gp, out, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
+    return reg_apply(ctx, dv, out, ctx->prob.alpha * ctx->wreg, ctx->prob.gamma, out);
+}
+
 lgnk_status precond_apply(lgnk_ctx* ctx, const float* r, float* z) {
     const int kd = ctx->K * ctx->d;
     cudaStream_t s = ctx->stream;
@@ -463,6 +580,7 @@ const char* lgnk_status_string(lgnk_status s) {
         case LGNK_ERR_INTERNAL: return "internal error";
         case LGNK_LS_FAILED: return "line search failed";
         case LGNK_NOT_CONVERGED: return "not converged (iteration cap)";
+        case LGNK_ERR_CAPACITY: return "a fixed capacity was exceeded";
     }
     return "unknown status";
 }
@@ -561,7 +679,9 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     if ((s = dalloc(ctx, ctx->Mv, &ctx->inv_eig)) != LGNK_OK) return fail(s);
     ctx->npartial = ctx->trace_blocks > 1280 ? ctx->trace_blocks : 1280;  // >= 2 x 608 min/max partials
     if ((s = dalloc(ctx, (size_t)ctx->npartial, &ctx->partial)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, (size_t)ctx->trace_blocks, &ctx->cpartial)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 8, &ctx->dres)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, 4, &ctx->fsc)) != LGNK_OK) return fail(s);
     if (cudaMallocHost((void**)&ctx->hres, 8 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         ctx->hres = nullptr;
@@ -680,6 +800,47 @@ lgnk_status lgnk_hessvec(lgnk_ctx* ctx, const float* v, const float* T, const fl
     return hessvec_packed(ctx, T, dv, Hdv);
 }
 
+lgnk_status lgnk_assemble(lgnk_ctx* ctx, const float* v, const float* T, size_t* blocks) {
+    CHECK_CTX();
+    ctx->asm_valid = false;
+    REQUIRE(v && T, "v and T must be non-NULL");
+    REQUIRE(ctx->prob.model == LGNK_TRANSPORT, "J is assembled for the transport model only");
+    TRY(pack_v(ctx, v, ctx->Vp));
+    TRY(pack_T(ctx, T));
+    TRY(assemble_packed(ctx));
+    if (blocks) *blocks = ctx->asm_entries;
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_jvp_assembled(lgnk_ctx* ctx, const float* dv, float* du) {
+    CHECK_CTX();
+    REQUIRE(dv && du && (const void*)dv != (const void*)du, "dv and du must be non-NULL and distinct");
+    REQUIRE(ctx->asm_valid, "no assembled J on this context (call lgnk_assemble)");
+    TRY(pack_v(ctx, dv, ctx->dVp));
+    EllArgs e = ell_args(ctx);
+    e.out = du;
+    return ell(ctx, ELL_JVP, e);
+}
+
+lgnk_status lgnk_jtvp_assembled(lgnk_ctx* ctx, const float* r, float* gv) {
+    CHECK_CTX();
+    REQUIRE(r && gv && (const void*)r != (const void*)gv, "r and gv must be non-NULL and distinct");
+    REQUIRE(ctx->asm_valid, "no assembled J on this context (call lgnk_assemble)");
+    TRY(zero_G(ctx));
+    EllArgs e = ell_args(ctx);
+    e.r = r;
+    TRY(ell(ctx, ELL_JTVP, e));
+    KL(launch_distribute_gradient(ctx->d, ctx->Gp, gv, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status lgnk_hessvec_assembled(lgnk_ctx* ctx, const float* dv, float* Hdv) {
+    CHECK_CTX();
+    REQUIRE(dv && Hdv && (const void*)dv != (const void*)Hdv, "dv and Hdv must be non-NULL and distinct");
+    REQUIRE(ctx->asm_valid, "no assembled J on this context (call lgnk_assemble)");
+    return hessvec_assembled_packed(ctx, dv, Hdv);
+}
+
 lgnk_status lgnk_jacobian_determinant(lgnk_ctx* ctx, const float* v, const float* T, float* det, double* det_min,
                                       double* det_max) {
     CHECK_CTX();
@@ -749,6 +910,7 @@ void lgnk_solve_opts_default(lgnk_solve_opts* o) {
     o->precond = 1;
     o->verbosity = 0;
     o->gn_grad_atol = 0.0;
+    o->matvec = 1;
 }
 
 lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts* opts_in,
@@ -760,7 +922,7 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
     lgnk_solve_opts_default(&o);
     if (opts_in) o = *opts_in;
     REQUIRE(o.max_gn >= 0 && o.max_pcg >= 1 && o.max_ls >= 1 && o.pcg_rtol > 0.0 && o.gn_grad_rtol >= 0.0 &&
-                o.gn_grad_atol >= 0.0,
+                o.gn_grad_atol >= 0.0 && (o.matvec == 0 || o.matvec == 1),
             "invalid solve options");
     const auto t_start = std::chrono::steady_clock::now();
     if (!ctx->have_solve) {
@@ -777,7 +939,27 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
     if (ctx->prob.model == LGNK_TRANSPORT) TRY(pack_T(ctx, T));
     TRY(pack_v(ctx, v, ctx->Vp));
     double J, D, S;
-    TRY(objective_packed(ctx, v, T, R, g, &J, &D, &S));
+    // With the assembled J (transport), one trace per accepted iterate yields
+    // the objective, the rows of J and, through them, the gradient; the PCG
+    // of the next GN step then reuses the rows.  Rows that do not fit (a
+    // capacity overflow, or no memory for them) fall back to the matrix-free
+    // products; no memory stops further attempts.
+    bool asm_off = !(o.matvec == 1 && ctx->prob.model == LGNK_TRANSPORT);
+    bool use_asm = false;
+    auto obj_grad = [&](const float* vv) -> lgnk_status {
+        use_asm = false;
+        if (!asm_off) {
+            const lgnk_status as = assemble_packed(ctx, vv, R, g, &J, &D, &S);
+            if (as == LGNK_OK) {
+                use_asm = true;
+                return LGNK_OK;
+            }
+            if (as != LGNK_ERR_CAPACITY && as != LGNK_ERR_OOM) return as;
+            asm_off = as == LGNK_ERR_OOM;
+        }
+        return objective_packed(ctx, vv, T, R, g, &J, &D, &S);
+    };
+    TRY(obj_grad(v));
     rep.objective_evals = 1;
     double gg;
     TRY(dot_host(ctx, g, g, n, &gg));
@@ -791,37 +973,46 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             status = LGNK_OK;
             break;
         }
+        if (use_asm) rep.assembled_gn++;
         // PCG on H x = -g from x = 0 (Eq. 11)
         CK(cudaMemsetAsync(x, 0, n * sizeof(float), s));
         KL(launch_add_scaled(r, g, -1.0f, g, 0.0f, n, s));
         if (o.precond) TRY(precond_apply(ctx, r, z));
         else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(p, z, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        double rz;
-        TRY(dot_host(ctx, r, z, n, &rz));
+        // The step lengths stay on the device (dres[5] = r.z, fsc = alpha,
+        // -alpha, beta); the host reads p.Hp and r.r once per iteration for
+        // the curvature and stopping tests, after the next direction is
+        // already enqueued.
+        const int nb = dot_blocks(n);
+        TRY(dot_dev(ctx, r, z, n, 5));
         int pit = 0;
         for (int i = 1; i <= o.max_pcg; ++i) {
-            TRY(hessvec_packed(ctx, T, p, Hp));
+            TRY(use_asm ? hessvec_assembled_packed(ctx, p, Hp) : hessvec_packed(ctx, T, p, Hp));
             rep.hessvecs++;
-            double pHp;
-            TRY(dot_host(ctx, p, Hp, n, &pHp));
-            if (!(pHp > 0.0)) {
+            TRY(dot_dev(ctx, p, Hp, n, 2));
+            KL(launch_pcg_scalars(ctx->dres, ctx->fsc, 0, s));
+            KL(launch_axpby_dev(0.0f, ctx->fsc + 0, p, 1.0f, nullptr, x, n, s));
+            KL(launch_axpby_dev(0.0f, ctx->fsc + 1, Hp, 1.0f, nullptr, r, n, s));
+            if (o.precond) TRY(precond_apply(ctx, r, z));
+            else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            KL(launch_dot2(r, r, z, n, ctx->partial, nb, s));
+            KL(launch_reduce(ctx->partial, nb, ctx->dres + 3, s));
+            KL(launch_reduce(ctx->partial + nb, nb, ctx->dres + 4, s));
+            KL(launch_pcg_scalars(ctx->dres, ctx->fsc, 1, s));
+            KL(launch_axpby_dev(1.0f, nullptr, z, 0.0f, ctx->fsc + 2, p, n, s));
+            TRY(fetch(ctx, 4));
+            const double pHp = ctx->hres[2], rr = ctx->hres[3];
+            if (!std::isfinite(pHp) || !std::isfinite(rr)) {
+                SETERR("non-finite inner product in PCG");
+                return LGNK_ERR_NUMERIC;
+            }
+            if (!(pHp > 0.0)) {     // alpha was 0: x and r are unchanged
                 if (pit == 0) CK(cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
                 break;
             }
-            const double a = rz / pHp;
-            KL(launch_axpby((float)a, p, 1.0f, x, n, s));
-            KL(launch_axpby((float)-a, Hp, 1.0f, r, n, s));
             pit = i;
-            double rr;
-            TRY(dot_host(ctx, r, r, n, &rr));
             if (std::sqrt(rr) <= o.pcg_rtol * gn) break;
-            if (o.precond) TRY(precond_apply(ctx, r, z));
-            else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-            double rzn;
-            TRY(dot_host(ctx, r, z, n, &rzn));
-            KL(launch_axpby(1.0f, z, (float)(rzn / rz), p, n, s));
-            rz = rzn;
         }
         rep.pcg_iters += pit;
         // Armijo backtracking on v + mu x (FP64 comparisons)
@@ -847,7 +1038,7 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             break;
         }
         CK(cudaMemcpyAsync(v, vt, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        TRY(objective_packed(ctx, v, T, R, g, &J, &D, &S));
+        TRY(obj_grad(v));
         rep.objective_evals++;
         TRY(dot_host(ctx, g, g, n, &gg));
         gn = std::sqrt(gg);

@@ -181,6 +181,50 @@ __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// Two inner products sharing the first operand in one pass: partial[b] =
+// sum a.b and partial[nblocks + b] = sum a.c over block b's slice.
+__global__ void dot2_kernel(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ c,
+                            size_t count, double* partial) {
+    double s = 0.0, t = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const double ai = (double)a[i];
+        s += ai * (double)b[i];
+        t += ai * (double)c[i];
+    }
+    s = block_reduce(s);
+    __syncthreads();          // block_reduce's shared slots are reused
+    t = block_reduce(t);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s;
+        partial[gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// PCG step lengths kept on the device (Eq. 11 solve): sc holds the FP64 inner
+// products [2] p.Hp, [3] r.r, [4] r.z (new), [5] r.z (current).
+//   mode 0: alpha = rz / pHp, or 0 when pHp is not positive; f[0] = alpha, f[1] = -alpha
+//   mode 1: beta = rz_new / rz, then rz = rz_new;             f[2] = beta
+__global__ void pcg_scalars_kernel(double* sc, float* f, int mode) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (mode == 0) {
+        const double php = sc[2];
+        const double a = php > 0.0 ? sc[5] / php : 0.0;
+        f[0] = (float)a;
+        f[1] = (float)-a;
+    } else {
+        f[2] = (float)(sc[4] / sc[5]);
+        sc[5] = sc[4];
+    }
+}
+
+// y = a x + b y, a = *ap when ap is given, b = *bp when bp is given.
+__global__ void axpby_dev_kernel(float a, const float* __restrict__ ap, const float* __restrict__ x, float b,
+                                 const float* __restrict__ bp, float* y, size_t count) {
+    const float ea = ap ? *ap : a, eb = bp ? *bp : b;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = fmaf(ea, x[i], eb * y[i]);
+}
+
 // Deterministic final sum of the per-block partials (one block).
 __global__ void reduce_kernel(const double* __restrict__ partial, int count, double* out) {
     double s = 0.0;
@@ -311,6 +355,83 @@ __global__ void dct_axis_kernel(const float* __restrict__ in, float* __restrict_
             for (int q = 0; q < m; ++q) acc = fmaf(__ldg(row + q), in[base + q * st], acc);
         }
         out[i] = acc;
+    }
+}
+
+// The same transform for axes of at most kDctTileMax cells, staged in shared
+// memory.  Each array block is viewed as [outer][m][inner] (inner = product
+// of the cell counts of the axes below `axis`).  A CTA transforms 32 lines:
+// 32 consecutive inner positions of one outer index (axis > 0), or 32
+// consecutive x rows (axis 0, inner = 1; the tile is transposed through
+// shared memory so that loads and stores stay coalesced).  The m x m matrix
+// (transposed for the inverse) sits in shared memory; warp w computes the
+// outputs k = w, w + 8, ... of all 32 lines, reading the matrix entry as a
+// broadcast and the tile without bank conflicts.
+constexpr int kDctTileMax = 128;
+constexpr int kDctLines = 32;
+constexpr int kDctRowsPerWarp = kDctTileMax / (kBlock / 32);
+
+template <bool XAXIS>
+__global__ void __launch_bounds__(kBlock) dct_tile_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                          const float* __restrict__ C, int m, long long inner,
+                                                          long long lines, int inverse) {
+    extern __shared__ float sm[];
+    float* Cs = sm;                   // [k][q]
+    float* tile = sm + m * m;         // [q][l], row stride kDctLines + 1
+    constexpr int TS = kDctLines + 1;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int e = t; e < m * m; e += kBlock) {
+        const int k = e / m, q = e % m;
+        Cs[e] = inverse ? __ldg(C + (size_t)q * m + k) : __ldg(C + e);
+    }
+    long long o = 0, i0 = 0, r0 = 0;
+    if (XAXIS) {
+        r0 = (long long)blockIdx.x * kDctLines;
+        for (int e = t; e < kDctLines * m; e += kBlock) {
+            const int l = e / m, q = e % m;
+            tile[q * TS + l] = (r0 + l < lines) ? __ldg(in + (size_t)(r0 + l) * m + q) : 0.0f;
+        }
+    } else {
+        o = blockIdx.y;
+        i0 = (long long)blockIdx.x * kDctLines;
+        for (int e = t; e < kDctLines * m; e += kBlock) {
+            const int q = e / kDctLines, l = e % kDctLines;
+            tile[q * TS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
+        }
+    }
+    __syncthreads();
+    float acc[kDctRowsPerWarp];
+#pragma unroll
+    for (int j = 0; j < kDctRowsPerWarp; ++j) acc[j] = 0.0f;
+#pragma unroll 4
+    for (int q = 0; q < m; ++q) {
+        const float x = tile[q * TS + lane];
+#pragma unroll
+        for (int j = 0; j < kDctRowsPerWarp; ++j) {
+            const int k = warp + 8 * j;
+            if (k < m) acc[j] = fmaf(Cs[k * m + q], x, acc[j]);
+        }
+    }
+    if (XAXIS) {
+        __syncthreads();              // the tile becomes the output stage [l][k]
+        float* stage = tile;
+        const int OS = m + 1;
+#pragma unroll
+        for (int j = 0; j < kDctRowsPerWarp; ++j) {
+            const int k = warp + 8 * j;
+            if (k < m) stage[lane * OS + k] = acc[j];
+        }
+        __syncthreads();
+        for (int e = t; e < kDctLines * m; e += kBlock) {
+            const int l = e / m, k = e % m;
+            if (r0 + l < lines) out[(size_t)(r0 + l) * m + k] = stage[l * OS + k];
+        }
+    } else if (i0 + lane < inner) {
+#pragma unroll
+        for (int j = 0; j < kDctRowsPerWarp; ++j) {
+            const int k = warp + 8 * j;
+            if (k < m) out[((size_t)o * m + k) * inner + i0 + lane] = acc[j];
+        }
     }
 }
 
@@ -552,6 +673,23 @@ int dot_blocks(size_t count) {
     return b < kReduceBlocks ? (b > 0 ? b : 1) : kReduceBlocks;
 }
 
+cudaError_t launch_dot2(const float* a, const float* b, const float* c, size_t count, double* partial, int nblocks,
+                        cudaStream_t s) {
+    dot2_kernel<<<nblocks, kBlock, 0, s>>>(a, b, c, count, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_scalars(double* sc, float* f, int mode, cudaStream_t s) {
+    pcg_scalars_kernel<<<1, 32, 0, s>>>(sc, f, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby_dev(float a, const float* ap, const float* x, float b, const float* bp, float* y,
+                             size_t count, cudaStream_t s) {
+    axpby_dev_kernel<<<grid_for(count), kBlock, 0, s>>>(a, ap, x, b, bp, y, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dot(const float* a, const float* b, size_t count, double* partial, int nblocks, cudaStream_t s) {
     dot_kernel<<<nblocks, kBlock, 0, s>>>(a, b, count, partial);
     return cudaGetLastError();
@@ -593,7 +731,50 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const D
                             int axis, bool inverse, cudaStream_t s) {
     (void)d;
     const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * nblocks_kd;
-    dct_axis_kernel<<<grid_for(total), kBlock, 0, s>>>(in, out, C, g, nblocks_kd, axis, inverse ? 1 : 0);
+    const int m = g.m[axis];
+    if (m > kDctTileMax) {
+        dct_axis_kernel<<<grid_for(total), kBlock, 0, s>>>(in, out, C, g, nblocks_kd, axis, inverse ? 1 : 0);
+        return cudaGetLastError();
+    }
+    // stage: the matrix plus a 32-line tile (also the transposed output stage of axis 0)
+    const size_t smem = ((size_t)m * m + (size_t)m * (kDctLines + 1) + kDctLines) * sizeof(float);
+    // the dynamic shared-memory limit is raised once per device and kernel
+    static bool attr_set_dev[64][2] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    bool* attr_set = attr_set_dev[dev];
+    const long long inner = axis == 0 ? 1 : (axis == 1 ? (long long)g.m[0] : (long long)g.m[0] * g.m[1]);
+    const long long outer = (long long)(total / ((size_t)m * inner));
+    if (axis == 0) {
+        if (!attr_set[0]) {
+            const cudaError_t e = cudaFuncSetAttribute(dct_tile_kernel<true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)(((size_t)kDctTileMax * kDctTileMax +
+                                                              (size_t)kDctTileMax * (kDctLines + 1) + kDctLines) *
+                                                             sizeof(float)));
+            if (e != cudaSuccess) return e;
+            attr_set[0] = true;
+        }
+        const long long rows = outer;   // inner = 1: every (y, z, block) is one line
+        dct_tile_kernel<true><<<(unsigned)((rows + kDctLines - 1) / kDctLines), kBlock, smem, s>>>(
+            in, out, C, m, 1, rows, inverse ? 1 : 0);
+    } else {
+        if (!attr_set[1]) {
+            const cudaError_t e = cudaFuncSetAttribute(dct_tile_kernel<false>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)(((size_t)kDctTileMax * kDctTileMax +
+                                                              (size_t)kDctTileMax * (kDctLines + 1) + kDctLines) *
+                                                             sizeof(float)));
+            if (e != cudaSuccess) return e;
+            attr_set[1] = true;
+        }
+        if (outer > 65535) {
+            dct_axis_kernel<<<grid_for(total), kBlock, 0, s>>>(in, out, C, g, nblocks_kd, axis, inverse ? 1 : 0);
+            return cudaGetLastError();
+        }
+        const dim3 grid((unsigned)((inner + kDctLines - 1) / kDctLines), (unsigned)outer);
+        dct_tile_kernel<false><<<grid, kBlock, smem, s>>>(in, out, C, m, inner, inner * m * outer, inverse ? 1 : 0);
+    }
     return cudaGetLastError();
 }
 

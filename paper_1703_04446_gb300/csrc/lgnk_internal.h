@@ -25,7 +25,7 @@ struct DevGrid {
     float inv_h[3];
 };
 
-enum TraceMode { MODE_FWD = 0, MODE_JVP = 1, MODE_JTVP = 2, MODE_HESS = 3, MODE_OBJGRAD = 4 };
+enum TraceMode { MODE_FWD = 0, MODE_JVP = 1, MODE_JTVP = 2, MODE_HESS = 3, MODE_OBJGRAD = 4, MODE_ASM = 5 };
 
 // Voxel tile of one 256-thread CTA of the tracing kernels (x, y, z).
 inline void trace_tile_shape(int d, int* t) {
@@ -66,7 +66,33 @@ struct TraceArgs {
     float* acc;               // continuity splat accumulator (padded image)
     void* G;                  // gradient accumulator slices [m][zp][yp][xp] of float4 (3D) / float2 (2D)
     double* partial;          // per-block FP64 partial sums of res^2
+    // MODE_ASM (transport): rows of the assembled J, entry-major [e][voxel]
+    long long* ekey;          // element of the lower corner of the entry's cell in the slice gradient space
+    float* eblk;              // [e][corner][component][voxel]: sum of w_corner * mu over the cell's stages
+    int* ecnt;                // entries per voxel
+    int* eflag;               // set to 1 when a row needs more than ewidth entries
+    double* cpartial;         // per-block sums of the entries per row (may be NULL)
+    int ewidth;               // entries per voxel the arrays hold
 };
+
+// Assembled J (transport): at most this many (slice, cell) blocks per row.
+inline int asm_capacity(int d) { return d == 3 ? 16 : 32; }
+
+// Products with the assembled J (one thread per voxel).
+enum EllMode { ELL_JVP = 0, ELL_JTVP = 1, ELL_HESS = 2 };
+struct EllArgs {
+    DevGrid vg;               // velocity grid (corner offsets in the padded slices)
+    long long M;              // voxels
+    const long long* ekey;
+    const float* eblk;
+    const int* ecnt;
+    const void* dV;           // pair-packed direction slices (JVP, HESS)
+    void* G;                  // slice gradient accumulator (JTVP, HESS)
+    const float* r;           // JTVP weights per voxel (ABI image layout)
+    float* out;               // JVP output (ABI image layout)
+    float cellvol;            // HESS weight h^d
+};
+cudaError_t launch_ell(int d, int mode, const EllArgs& a, cudaStream_t s);
 
 // trace kernels (trace2d.cu / trace3d.cu)
 cudaError_t launch_trace(int d, bool nonstat, int model, int mode, const TraceArgs& a, int nblocks,
@@ -93,6 +119,13 @@ cudaError_t launch_reduce(const double* partial, int count, double* out, cudaStr
 cudaError_t launch_dot(const float* a, const float* b, size_t count, double* partial, int nblocks,
                        cudaStream_t s);
 int dot_blocks(size_t count);
+// partial[0..nblocks) = a.b, partial[nblocks..2 nblocks) = a.c (per-block FP64 sums)
+cudaError_t launch_dot2(const float* a, const float* b, const float* c, size_t count, double* partial, int nblocks,
+                        cudaStream_t s);
+// PCG step lengths from device inner products (see grid_ops.cu)
+cudaError_t launch_pcg_scalars(double* sc, float* f, int mode, cudaStream_t s);
+cudaError_t launch_axpby_dev(float a, const float* ap, const float* x, float b, const float* bp, float* y,
+                             size_t count, cudaStream_t s);
 // out = addsrc + scale * A x + gamma * x for the Neumann Laplacian A = B^T B of each
 // (time node, component) block; addsrc may be NULL or equal to out.
 cudaError_t launch_laplacian(int d, const float* x, float* out, const DevGrid& g, int blocks_kd,

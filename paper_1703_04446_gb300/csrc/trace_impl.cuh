@@ -14,6 +14,11 @@
 //            voxel (u1 at voxel i depends only on characteristic i, so the
 //            JVP value feeds that voxel's JTVP seed directly).
 //   OBJGRAD  transport only: u1, SSD partials and the JTVP of h^d res fused.
+//   ASM      transport only: the adjoint sweep seeded with grad T(y) yields
+//            row i of J = d_v u1 (Sec. 3.3 assembles J as a sparse matrix);
+//            its stage contributions are summed per (slice, cell) block in a
+//            per-thread table and written out entry-major (ELL layout), and
+//            ell_kernel then applies J, J^T and J^T h^d J.
 //
 // Position representation.  A characteristic starts at a cell centre x_c and
 // its state is the FP32 displacement u = y - x_c.  Looking a point up on a grid
@@ -46,6 +51,8 @@
 // slower: float atomics on shared memory retry under the heavy same-address
 // contention of neighbouring characteristics.
 #pragma once
+
+#include <type_traits>
 
 #include "lgnk_internal.h"
 
@@ -340,10 +347,72 @@ __device__ __forceinline__ void scatter_add(const DevGrid& g, Scatter<D>& S, siz
     }
 }
 
+template <int D>
+__device__ __forceinline__ void scatter_init(Scatter<D>& S, void* G) {
+    S.G = static_cast<typename VecT<D>::type*>(G);
+    S.base = -1;
+    S.s0 = 0;
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_finish(const DevGrid& g, Scatter<D>& S) {
+    if (S.base >= 0) scatter_flush<D>(g, S, false, S.f, S.mu);
+}
+
+// Destination of the adjoint contributions when a row of J is assembled: a
+// per-thread table of (slice, cell) blocks, each the 2^d corner vectors
+// sum_stages w_c(f) mu.  A trajectory stays within a few velocity cells, so a
+// row has few blocks; a row that needs more than CAP sets `overflow`.
+template <int D>
+struct AsmRow {
+    static constexpr int CAP = D == 3 ? 16 : 32;
+    long long key[CAP];
+    float blk[CAP][(1 << D) * D];
+    int n;
+    bool overflow;
+};
+
+template <int D>
+__device__ __forceinline__ void scatter_init(AsmRow<D>& S, void*) {
+    S.n = 0;
+    S.overflow = false;
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_finish(const DevGrid&, AsmRow<D>&) {}
+
+template <int D>
+__device__ __forceinline__ void scatter_add(const DevGrid& g, AsmRow<D>& S, size_t s0, int base, const float* f,
+                                            const float* mu) {
+    (void)g;
+    const long long key = (long long)s0 + base;
+    int j = S.n - 1;
+#pragma unroll 1
+    for (; j >= 0; --j)       // newest first: a trajectory revisits the cell it just left
+        if (S.key[j] == key) break;
+    if (j < 0) {
+        if (S.n == AsmRow<D>::CAP) {
+            S.overflow = true;
+            return;
+        }
+        j = S.n++;
+        S.key[j] = key;
+#pragma unroll
+        for (int k = 0; k < (1 << D) * D; ++k) S.blk[j][k] = 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        float w = (c & 1 ? f[0] : 1.0f - f[0]) * ((c >> 1) & 1 ? f[1] : 1.0f - f[1]);
+        if (D == 3) w *= ((c >> 2) & 1) ? f[D - 1] : 1.0f - f[D - 1];
+#pragma unroll
+        for (int q = 0; q < D; ++q) S.blk[j][c * D + q] = fmaf(w, mu[q], S.blk[j][c * D + q]);
+    }
+}
+
 // Adjoint stage: scatter w_c mu into the slice's gradient and return
 // nu = d_y I(v, y, t)^T mu = grad_y (v . mu) of the interpolant.
-template <int D>
-__device__ __forceinline__ void stage_adjoint(const DevGrid& g, const float* __restrict__ V, Scatter<D>& S,
+template <int D, class SC>
+__device__ __forceinline__ void stage_adjoint(const DevGrid& g, const float* __restrict__ V, SC& S,
                                               size_t s0, const int* p, const float* f, const float* mu, float* nu) {
     const int base = linear<D>(g, p);
     float s_0, dx, dy;
@@ -629,8 +698,8 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
 // scatter the step's contribution into the gradient and return the adjoint of
 // its start.  The stage positions u, u2, u3, u4 were recorded by the forward
 // sweep; each stage's J^T mu and scatter share one pass over its corners.
-template <int D, bool NS>
-__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, Scatter<D>& S, const float* rec,
+template <int D, bool NS, class SC>
+__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, SC& S, const float* rec,
                                                  float* lam, int k) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
@@ -645,24 +714,154 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float
 #pragma unroll
     for (int a = 0; a < D; ++a) { mu[a] = c16 * lam[a]; us[a] = rec[3 * D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D>(A.vg, V, S, s4, p, f, mu, nu);
+    stage_adjoint<D, SC>(A.vg, V, S, s4, p, f, mu, nu);
     // stage 3: D3 = I(dv, y3) + J3 (dy + dt/2 D2)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); us[a] = rec[2 * D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D>(A.vg, V, S, s2, p, f, mu, nu);
+    stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 2: D2 = I(dv, y2) + J2 (dy + dt/2 D1)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); us[a] = rec[D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D>(A.vg, V, S, s2, p, f, mu, nu);
+    stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 1: D1 = I(dv, y) + J1 dy
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); us[a] = rec[a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D>(A.vg, V, S, s1, p, f, mu, nu);
+    stage_adjoint<D, SC>(A.vg, V, S, s1, p, f, mu, nu);
 #pragma unroll
     for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
+}
+
+// Store one assembled row entry-major: the key of entry e of voxel i at
+// [e][i], its block of 2^d corner vectors contiguous at [e][i][corner][q]
+// (96 bytes in 3D, 32 in 2D), so a warp streams one contiguous range per entry.
+template <int D>
+__device__ __forceinline__ void write_row(const TraceArgs& A, const AsmRow<D>& S, int vox) {
+    const long long M = (long long)A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
+    if (S.overflow || S.n > A.ewidth) {
+        A.ecnt[vox] = 0;
+        atomicExch(A.eflag, 1);
+        return;
+    }
+    A.ecnt[vox] = S.n;
+    constexpr int B = (1 << D) * D;
+#pragma unroll 1
+    for (int j = 0; j < S.n; ++j) {
+        A.ekey[j * M + vox] = S.key[j];
+        float4* dst = reinterpret_cast<float4*>(A.eblk + ((size_t)j * M + vox) * B);
+#pragma unroll
+        for (int k = 0; k < B / 4; ++k)
+            dst[k] = make_float4(S.blk[j][4 * k], S.blk[j][4 * k + 1], S.blk[j][4 * k + 2], S.blk[j][4 * k + 3]);
+    }
+}
+
+// Products with the assembled J, one thread per voxel i (row i):
+//   ELL_JVP   out_i = J_i dv = sum_e sum_c blk_e[c] . dV[key_e + corner c]
+//   ELL_JTVP  G[key_e + corner c] += r_i blk_e[c]
+//   ELL_HESS  both, with the weight h^d (J_i dv) (the Gauss-Newton data term)
+// Most rows have one block: the first is loaded without waiting for the row
+// length (every row has at least one) and kept in registers for both the
+// gather and the scatter; further blocks are read in a loop (twice for HESS).
+constexpr int kEllRegBlocks = 1;
+
+template <int D>
+__device__ __forceinline__ void ell_load(const EllArgs& A, long long i, int j, long long& key, float* b) {
+    constexpr int B = (1 << D) * D;
+    key = __ldg(A.ekey + j * A.M + i);
+    const float4* p = reinterpret_cast<const float4*>(A.eblk + ((size_t)j * A.M + i) * B);
+#pragma unroll
+    for (int k = 0; k < B / 4; ++k) {
+        const float4 t = __ldg(p + k);
+        b[4 * k] = t.x;
+        b[4 * k + 1] = t.y;
+        b[4 * k + 2] = t.z;
+        b[4 * k + 3] = t.w;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float ell_dot(const EllArgs& A, const float* __restrict__ dV, long long key, const float* b) {
+    float s = 0.0f;
+#pragma unroll
+    for (int r = 0; r < (1 << (D - 1)); ++r) {     // rows of x-pairs (cy, cz); corner (0, cy, cz) is 2 r
+        float lo[3], hi[3];
+        pair_value<D>(dV, corner_elem<D>(A.vg, (size_t)key, 0, 0, r & 1, r >> 1), lo, hi);
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            s = fmaf(b[2 * r * D + q], lo[q], s);
+            s = fmaf(b[(2 * r + 1) * D + q], hi[q], s);
+        }
+    }
+    return s;
+}
+
+template <int D>
+__device__ __forceinline__ void ell_scatter(const EllArgs& A, long long key, const float* b, float w) {
+    using VT = typename VecT<D>::type;
+    VT* G = static_cast<VT*>(A.G);
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c)
+        red_vec(G + corner_elem<D>(A.vg, (size_t)key, 0, c & 1, (c >> 1) & 1, (c >> 2) & 1), b + c * D, w);
+}
+
+template <int D, int EMODE>
+__global__ void __launch_bounds__(LGNK_BLOCK) ell_kernel(const EllArgs A) {
+    constexpr int B = (1 << D) * D;
+    constexpr int RB = kEllRegBlocks;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.M) return;
+    const float* dV = static_cast<const float*>(A.dV);
+    const int n = __ldg(A.ecnt + i);
+    long long kr[RB > 0 ? RB : 1];
+    float br[RB > 0 ? RB : 1][B];
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+        if (j == 0 || j < n) ell_load<D>(A, i, j, kr[j], br[j]);
+    float s = 0.0f;
+    if (EMODE != ELL_JTVP) {
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+            if (j < n) s += ell_dot<D>(A, dV, kr[j], br[j]);
+#pragma unroll 1
+        for (int j = RB; j < n; ++j) {
+            long long k;
+            float b[B];
+            ell_load<D>(A, i, j, k, b);
+            s += ell_dot<D>(A, dV, k, b);
+        }
+        if (EMODE == ELL_JVP) {
+            A.out[i] = s;
+            return;
+        }
+        s *= A.cellvol;
+    } else {
+        s = A.r[i];
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+        if (j < n) ell_scatter<D>(A, kr[j], br[j], s);
+#pragma unroll 1
+    for (int j = RB; j < n; ++j) {
+        long long k;
+        float b[B];
+        ell_load<D>(A, i, j, k, b);
+        ell_scatter<D>(A, k, b, s);
+    }
+}
+
+template <int D>
+static cudaError_t launch_ell_dim(int mode, const EllArgs& a, cudaStream_t s) {
+    const long long blocks = (a.M + LGNK_BLOCK - 1) / LGNK_BLOCK;
+    if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    switch (mode) {
+        case ELL_JVP: ell_kernel<D, ELL_JVP><<<(unsigned)blocks, LGNK_BLOCK, 0, s>>>(a); break;
+        case ELL_JTVP: ell_kernel<D, ELL_JTVP><<<(unsigned)blocks, LGNK_BLOCK, 0, s>>>(a); break;
+        case ELL_HESS: ell_kernel<D, ELL_HESS><<<(unsigned)blocks, LGNK_BLOCK, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 __device__ __forceinline__ double block_sum(double x) {
@@ -689,7 +888,8 @@ template <int D, bool NS, int MODEL, int MODE>
 __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_kernel(const TraceArgs A) {
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
-    constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD);
+    constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD || MODE == MODE_ASM);
+    using SC = typename std::conditional<MODE == MODE_ASM, AsmRow<D>, Scatter<D>>::type;
     const float* V = static_cast<const float*>(A.V);
     const float* dV = static_cast<const float*>(A.dV);
 
@@ -697,11 +897,10 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_ke
     voxel_index<D>(A, idx);
     const bool active = idx[0] < A.ig.m[0] && idx[1] < A.ig.m[1] && (D == 2 || idx[2] < A.ig.m[2]);
     double ssd = 0.0;
+    double entries = 0.0;     // MODE_ASM: blocks of this thread's row
 
-    Scatter<D> S;
-    S.G = static_cast<VT*>(A.G);
-    S.base = -1;
-    S.s0 = 0;
+    SC S;
+    scatter_init<D>(S, A.G);
 
     if (active) {
         const int vox = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
@@ -760,6 +959,15 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_ke
                 const float s = A.cellvol * du;
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = s * gT[a];
+            } else if (MODE == MODE_ASM) {
+                const float val = sample_image<D, true>(A.ig, si, A.Tp, u, gT);
+#pragma unroll
+                for (int a = 0; a < D; ++a) lam[a] = gT[a];
+                if (A.R != nullptr) {     // with the objective: SSD and the gradient's weights h^d res
+                    const double rd = (double)val - (double)A.R[vox];
+                    ssd = rd * rd;
+                    A.u1[vox] = A.cellvol * (float)rd;
+                }
             } else {  // MODE_OBJGRAD
                 const float val = sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 if (A.u1 != nullptr) A.u1[vox] = val;
@@ -796,16 +1004,25 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_ke
 
         if (ADJOINT) {
 #pragma unroll 1
-            for (int k = A.N - 1; k >= 0; --k) rk4_adjoint_step<D, NS>(A, V, S, hist[ADJOINT ? k : 0], lam, k);
-            if (S.base >= 0) scatter_flush<D>(A.vg, S, false, S.f, S.mu);
+            for (int k = A.N - 1; k >= 0; --k) rk4_adjoint_step<D, NS, SC>(A, V, S, hist[ADJOINT ? k : 0], lam, k);
+            scatter_finish<D>(A.vg, S);
+            if constexpr (MODE == MODE_ASM) {
+                write_row<D>(A, S, vox);
+                entries = (double)S.n;
+            }
         }
     }
 
-    if (MODE == MODE_OBJGRAD || MODE == MODE_FWD) {
+    if (MODE == MODE_OBJGRAD || MODE == MODE_FWD || MODE == MODE_ASM) {
         if (A.partial != nullptr) {
             const double s = block_sum(ssd);
             if (threadIdx.x == 0) A.partial[blockIdx.x] = s;
         }
+    }
+    if (MODE == MODE_ASM && A.cpartial != nullptr) {
+        __syncthreads();      // block_sum's shared slots are reused
+        const double c = block_sum(entries);
+        if (threadIdx.x == 0) A.cpartial[blockIdx.x] = c;
     }
 }
 
@@ -831,6 +1048,7 @@ static cudaError_t launch_dim(int model, int mode, const TraceArgs& a, int nbloc
             case MODE_JTVP: return launch_one<D, NS, LGNK_TRANSPORT, MODE_JTVP>(a, nblocks, s);
             case MODE_HESS: return launch_one<D, NS, LGNK_TRANSPORT, MODE_HESS>(a, nblocks, s);
             case MODE_OBJGRAD: return launch_one<D, NS, LGNK_TRANSPORT, MODE_OBJGRAD>(a, nblocks, s);
+            case MODE_ASM: return launch_one<D, NS, LGNK_TRANSPORT, MODE_ASM>(a, nblocks, s);
         }
     } else {
         switch (mode) {

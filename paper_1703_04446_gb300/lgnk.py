@@ -27,7 +27,7 @@ _MODELS = {"transport": TRANSPORT, "continuity": CONTINUITY}
 _REGS = {"diffusion": DIFFUSION, "curvature": CURVATURE, "elastic": ELASTIC}
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "non-finite value",
-          5: "internal error", 6: "line search failed", 7: "not converged"}
+          5: "internal error", 6: "line search failed", 7: "not converged", 8: "capacity exceeded"}
 
 
 class LgnkError(RuntimeError):
@@ -51,14 +51,16 @@ class _Problem(ctypes.Structure):
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("max_gn", ctypes.c_int), ("gn_grad_rtol", ctypes.c_double), ("max_pcg", ctypes.c_int),
                 ("pcg_rtol", ctypes.c_double), ("armijo_c", ctypes.c_double), ("max_ls", ctypes.c_int),
-                ("precond", ctypes.c_int), ("verbosity", ctypes.c_int), ("gn_grad_atol", ctypes.c_double)]
+                ("precond", ctypes.c_int), ("verbosity", ctypes.c_int), ("gn_grad_atol", ctypes.c_double),
+                ("matvec", ctypes.c_int)]
 
 
 class _SolveReport(ctypes.Structure):
     _fields_ = [("gn_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("hessvecs", ctypes.c_int),
                 ("objective_evals", ctypes.c_int), ("J0", ctypes.c_double), ("J", ctypes.c_double),
                 ("D", ctypes.c_double), ("S", ctypes.c_double), ("g0", ctypes.c_double),
-                ("g", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+                ("g", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
+                ("assembled_gn", ctypes.c_int)]
 
 
 EXPORTS = {
@@ -77,6 +79,10 @@ EXPORTS = {
                        + [ctypes.c_void_p]),
     "lgnk_hessvec": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "lgnk_precond": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "lgnk_assemble": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.POINTER(ctypes.c_size_t)]),
+    "lgnk_jvp_assembled": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "lgnk_jtvp_assembled": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "lgnk_hessvec_assembled": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "lgnk_jacobian_determinant": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.POINTER(ctypes.c_double)] * 2),
     "lgnk_dot": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
     "lgnk_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -284,6 +290,18 @@ class Context:
     def precond(self, r):
         return lgnk_precond(self, r)
 
+    def assemble(self, v, T):
+        return lgnk_assemble(self, v, T)
+
+    def jvp_assembled(self, dv):
+        return lgnk_jvp_assembled(self, dv)
+
+    def jtvp_assembled(self, r):
+        return lgnk_jtvp_assembled(self, r)
+
+    def hessvec_assembled(self, dv, out=None):
+        return lgnk_hessvec_assembled(self, dv, out)
+
     def jacobian_determinant(self, v, T, field=True):
         return lgnk_jacobian_determinant(self, v, T, field)
 
@@ -358,6 +376,43 @@ def lgnk_hessvec(ctx: Context, v, T, dv, out=None):
     out = ctx._new_vel() if out is None else ctx._vel(out, "out")
     ctx._stream()
     ctx._check(ctx.lib.lgnk_hessvec(ctx.handle, _ptr(v), _ptr(T), _ptr(dv), _ptr(out)))
+    return out
+
+
+def lgnk_assemble(ctx: Context, v, T):
+    """Assemble J = d_v u1 at (v, T) (transport, Sec. 3.3) into the context.
+    Returns the number of (time slice, velocity cell) blocks stored."""
+    ctx._vel(v, "v"), ctx._img(T, "T")
+    blocks = ctypes.c_size_t()
+    ctx._stream()
+    ctx._check(ctx.lib.lgnk_assemble(ctx.handle, _ptr(v), _ptr(T), ctypes.byref(blocks)))
+    return blocks.value
+
+
+def lgnk_jvp_assembled(ctx: Context, dv):
+    """J dv with the assembled J."""
+    ctx._vel(dv, "dv")
+    du = ctx._new_img()
+    ctx._stream()
+    ctx._check(ctx.lib.lgnk_jvp_assembled(ctx.handle, _ptr(dv), _ptr(du)))
+    return du
+
+
+def lgnk_jtvp_assembled(ctx: Context, r):
+    """J^T r with the assembled J."""
+    ctx._img(r, "r")
+    gv = ctx._new_vel()
+    ctx._stream()
+    ctx._check(ctx.lib.lgnk_jtvp_assembled(ctx.handle, _ptr(r), _ptr(gv)))
+    return gv
+
+
+def lgnk_hessvec_assembled(ctx: Context, dv, out=None):
+    """Gauss-Newton Hessian matvec with the assembled J (plus the regularizer)."""
+    ctx._vel(dv, "dv")
+    out = ctx._new_vel() if out is None else ctx._vel(out, "out")
+    ctx._stream()
+    ctx._check(ctx.lib.lgnk_hessvec_assembled(ctx.handle, _ptr(dv), _ptr(out)))
     return out
 
 

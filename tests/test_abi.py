@@ -42,8 +42,8 @@ def test_binding_declares_every_symbol():
 
 
 def test_status_strings(lib):
-    for s in range(8):
-        assert lib.lgnk_status_string(s)
+    for s in range(9):
+        assert lib.lgnk_status_string(s) != b"unknown status"
     assert lib.lgnk_status_string(99) == b"unknown status"
 
 
@@ -95,6 +95,9 @@ def test_null_context_is_rejected(lib):
     for name in ("lgnk_forward", "lgnk_jvp", "lgnk_jtvp", "lgnk_hessvec"):
         assert getattr(lib, name)(None, None, None, None, None) == 1
     assert lib.lgnk_precond(None, None, None) == 1
+    assert lib.lgnk_assemble(None, None, None, None) == 1
+    for name in ("lgnk_jvp_assembled", "lgnk_jtvp_assembled", "lgnk_hessvec_assembled"):
+        assert getattr(lib, name)(None, None, None) == 1
     lib.lgnk_destroy(None)
     assert lib.lgnk_scratch_bytes(None) == 0
 

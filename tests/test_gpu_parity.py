@@ -94,6 +94,22 @@ def test_preconditioner(name):
     assert rel(_np(ctx.precond(t["dv"])), _oracle(name)["prec"]) <= TOL
 
 
+@pytest.mark.parametrize("vm,K", [((130, 20), 2), ((40, 36, 129), 1), ((128, 128), 1)])
+def test_preconditioner_axis_lengths(vm, K):
+    """Axes of more than 128 cells take the untiled DCT kernel, the others the
+    shared-memory tile (128 is the largest tiled length)."""
+    from oracle import lagrangian as Lg
+    from oracle.objective import Problem as OProblem
+    from paper_1703_04446_gb300 import lgnk
+    d = len(vm)
+    im = tuple(2 * a for a in vm)
+    op = OProblem(Lg.Grid(im), Lg.Grid(vm), K=K, N=2, alpha=1e-2, gamma=1e-3)
+    ctx = lgnk.Context(lgnk.Problem(image_m=im, velocity_m=vm, time_nodes=K, rk4_steps=2, alpha=1e-2, gamma=1e-3))
+    r = np.random.default_rng(3).normal(size=(K, d) + tuple(reversed(vm))).astype(np.float32)
+    got = _np(ctx.precond(torch.from_numpy(r).cuda()))
+    assert rel(got, apply_preconditioner(op, r.astype(np.float64))) <= TOL
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_adjoint_identity_on_gpu(name):
     """<J dv, r> = <dv, J^T r> within FP32 accumulation error."""
