@@ -50,6 +50,10 @@ struct lgnk_ctx {
     double* dres = nullptr;
     double* hres = nullptr;       // pinned host mirror of dres
     float* fsc = nullptr;         // PCG step lengths on the device (alpha, -alpha, beta)
+    // lgnk_solve runs on a stream of its own (capturable, unlike the legacy
+    // default stream), ordered after and before the caller's stream by events
+    cudaStream_t solve_stream = nullptr;
+    cudaEvent_t ev_enter = nullptr, ev_leave = nullptr;
     float* sv[7] = {nullptr};
     bool have_solve = false;
     float* ybuf = nullptr;        // end points [d][M] for lgnk_jacobian_determinant
@@ -596,6 +600,9 @@ size_t lgnk_scratch_bytes(const lgnk_ctx* ctx) {
 void lgnk_destroy(lgnk_ctx* ctx) {
     if (ctx == nullptr) return;
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->ev_enter) cudaEventDestroy(ctx->ev_enter);
+    if (ctx->ev_leave) cudaEventDestroy(ctx->ev_leave);
+    if (ctx->solve_stream) cudaStreamDestroy(ctx->solve_stream);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->hres) cudaFreeHost(ctx->hres);
     delete ctx;
@@ -913,17 +920,20 @@ void lgnk_solve_opts_default(lgnk_solve_opts* o) {
     o->matvec = 1;
 }
 
-lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts* opts_in,
+// One PCG iteration's device work as a replayable CUDA graph (one per
+// matvec variant and solve).  Captured on first use; the launches it holds
+// are counted on every replay.
+struct PcgGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0, trace_launches = 0;
+    bool failed = false;
+    ~PcgGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts& o,
                        lgnk_solve_report* rep_out) {
-    CHECK_CTX();
-    REQUIRE(T && R && v, "T, R and v_inout must be non-NULL");
-    REQUIRE(distinct(v, {T, R}), "v_inout must not alias T or R");
-    lgnk_solve_opts o;
-    lgnk_solve_opts_default(&o);
-    if (opts_in) o = *opts_in;
-    REQUIRE(o.max_gn >= 0 && o.max_pcg >= 1 && o.max_ls >= 1 && o.pcg_rtol > 0.0 && o.gn_grad_rtol >= 0.0 &&
-                o.gn_grad_atol >= 0.0 && (o.matvec == 0 || o.matvec == 1),
-            "invalid solve options");
     const auto t_start = std::chrono::steady_clock::now();
     if (!ctx->have_solve) {
         for (int i = 0; i < 7; ++i) TRY(dalloc(ctx, ctx->n, &ctx->sv[i]));
@@ -933,6 +943,7 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
           *vt = ctx->sv[6];
     const size_t n = ctx->n;
     cudaStream_t s = ctx->stream;
+    PcgGraph graphs[2];           // [0] matrix-free, [1] assembled
     lgnk_solve_report rep;
     memset(&rep, 0, sizeof(rep));
 
@@ -986,10 +997,11 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
         // already enqueued.
         const int nb = dot_blocks(n);
         TRY(dot_dev(ctx, r, z, n, 5));
-        int pit = 0;
-        for (int i = 1; i <= o.max_pcg; ++i) {
+        // CUDA graphs need a capturable stream and no per-launch profiling events
+        const bool use_graphs = !ctx->prof && s == ctx->solve_stream && s != nullptr;
+        // the device work of one iteration; ends with p.Hp and r.r in hres[2], hres[3]
+        auto body = [&]() -> lgnk_status {
             TRY(use_asm ? hessvec_assembled_packed(ctx, p, Hp) : hessvec_packed(ctx, T, p, Hp));
-            rep.hessvecs++;
             TRY(dot_dev(ctx, p, Hp, n, 2));
             KL(launch_pcg_scalars(ctx->dres, ctx->fsc, 0, s));
             KL(launch_axpby_dev(0.0f, ctx->fsc + 0, p, 1.0f, nullptr, x, n, s));
@@ -1001,7 +1013,44 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             KL(launch_reduce(ctx->partial + nb, nb, ctx->dres + 4, s));
             KL(launch_pcg_scalars(ctx->dres, ctx->fsc, 1, s));
             KL(launch_axpby_dev(1.0f, nullptr, z, 0.0f, ctx->fsc + 2, p, n, s));
-            TRY(fetch(ctx, 4));
+            CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            return LGNK_OK;
+        };
+        PcgGraph& gr = graphs[use_asm ? 1 : 0];
+        int pit = 0;
+        for (int i = 1; i <= o.max_pcg; ++i) {
+            if (use_graphs && gr.exec == nullptr && !gr.failed) {
+                // capture; any failure ends the capture and falls back to direct launches
+                const long long l0 = ctx->launches, t0 = ctx->trace_launches;
+                cudaGraph_t graph = nullptr;
+                bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    ok = body() == LGNK_OK;
+                    ok = (cudaStreamEndCapture(s, &graph) == cudaSuccess) && ok && graph != nullptr;
+                }
+                if (ok) ok = cudaGraphInstantiate(&gr.exec, graph, 0) == cudaSuccess;
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                gr.launches = ctx->launches - l0;
+                gr.trace_launches = ctx->trace_launches - t0;
+                ctx->launches = l0;
+                ctx->trace_launches = t0;
+                if (!ok) {
+                    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+                    gr.exec = nullptr;
+                    gr.failed = true;
+                    ctx->err[0] = 0;
+                }
+            }
+            if (gr.exec != nullptr) {
+                CK(cudaGraphLaunch(gr.exec, s));
+                ctx->launches += gr.launches;
+                ctx->trace_launches += gr.trace_launches;
+            } else {
+                TRY(body());
+            }
+            CK(cudaStreamSynchronize(s));
+            rep.hessvecs++;
             const double pHp = ctx->hres[2], rr = ctx->hres[3];
             if (!std::isfinite(pHp) || !std::isfinite(rr)) {
                 SETERR("non-finite inner product in PCG");
@@ -1056,6 +1105,35 @@ lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
     rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (rep_out) *rep_out = rep;
     return status;
+}
+
+lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts* opts_in,
+                       lgnk_solve_report* rep_out) {
+    CHECK_CTX();
+    REQUIRE(T && R && v, "T, R and v_inout must be non-NULL");
+    REQUIRE(distinct(v, {T, R}), "v_inout must not alias T or R");
+    lgnk_solve_opts o;
+    lgnk_solve_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    REQUIRE(o.max_gn >= 0 && o.max_pcg >= 1 && o.max_ls >= 1 && o.pcg_rtol > 0.0 && o.gn_grad_rtol >= 0.0 &&
+                o.gn_grad_atol >= 0.0 && (o.matvec == 0 || o.matvec == 1),
+            "invalid solve options");
+    if (ctx->solve_stream == nullptr) {
+        CK(cudaStreamCreateWithFlags(&ctx->solve_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_enter, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_leave, cudaEventDisableTiming));
+    }
+    // run on the context's own stream, after the caller's pending work; the
+    // caller's stream waits for everything the solve enqueued, also on error
+    cudaStream_t user = ctx->stream;
+    CK(cudaEventRecord(ctx->ev_enter, user));
+    CK(cudaStreamWaitEvent(ctx->solve_stream, ctx->ev_enter, 0));
+    ctx->stream = ctx->solve_stream;
+    const lgnk_status st = solve_impl(ctx, T, R, v, o, rep_out);
+    ctx->stream = user;
+    CK(cudaEventRecord(ctx->ev_leave, ctx->solve_stream));
+    CK(cudaStreamWaitEvent(user, ctx->ev_leave, 0));
+    return st;
 }
 
 lgnk_status lgnk_restrict_image(const lgnk_grid* fine, const float* F, float* C, void* stream) {
