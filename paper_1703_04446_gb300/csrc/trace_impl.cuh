@@ -429,6 +429,112 @@ __device__ __forceinline__ void stage_adjoint(const DevGrid& g, const float* __r
     scatter_add<D>(g, S, s0, base, f, mu);
 }
 
+// The 2^d corner vectors of the velocity cell last met (and of the direction
+// when DV), kept in registers: consecutive RK4 stages mostly fall in the same
+// cell and slice (stages 2 and 3 share their time and nearly their position,
+// stage 4 of a step is stage 1 of the next), so a stage reloads them only
+// when its cell or slice changes.  Corner c = cx + 2 cy + 4 cz.
+template <int D, bool DV>
+struct CellCache {
+    long long key;            // s0 + base of the cached cell, -1 when empty
+    float v[1 << D][D];
+    float dv[DV ? (1 << D) : 1][D];
+};
+
+template <int D, bool DV>
+__device__ __forceinline__ void cache_cell(const DevGrid& g, const float* __restrict__ V, const float* __restrict__ dV,
+                                           size_t s0, int base, CellCache<D, DV>& C) {
+    const long long key = (long long)s0 + base;
+    if (key == C.key) return;
+    C.key = key;
+#pragma unroll
+    for (int r = 0; r < (1 << (D - 1)); ++r) {
+        pair_value<D>(V, corner_elem<D>(g, s0, base, 0, r & 1, r >> 1), C.v[2 * r], C.v[2 * r + 1]);
+        if (DV) pair_value<D>(dV, corner_elem<D>(g, s0, base, 0, r & 1, r >> 1), C.dv[2 * r], C.dv[2 * r + 1]);
+    }
+}
+
+// The cached-cell forms of stage_tangent and stage_adjoint below (same
+// arithmetic in the same order).
+template <int D>
+__device__ __forceinline__ void cell_plane(const float (*c)[D], int z, const float* f, int q, float& val, float& dx,
+                                           float& dy) {
+    const float* c00 = c[4 * z];
+    const float* c10 = c[4 * z + 1];
+    const float* c01 = c[4 * z + 2];
+    const float* c11 = c[4 * z + 3];
+    const float a0 = lerp(c00[q], c10[q], f[0]);
+    const float a1 = lerp(c01[q], c11[q], f[0]);
+    val = lerp(a0, a1, f[1]);
+    dx = lerp(c10[q] - c00[q], c11[q] - c01[q], f[1]);
+    dy = a1 - a0;
+}
+
+template <int D>
+__device__ __forceinline__ void stage_tangent_cached(const DevGrid& g, const float* __restrict__ V,
+                                                     const float* __restrict__ dV, size_t s0, const int* p,
+                                                     const float* f, const float* qv, CellCache<D, true>& C,
+                                                     float* val, float* Jq, float* dval) {
+    cache_cell<D, true>(g, V, dV, s0, linear<D>(g, p), C);
+    float qs[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) qs[a] = qv[a] * g.inv_h[a];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        float v0, dx, dy, w0, e0, e1;
+        cell_plane<D>(C.v, 0, f, q, v0, dx, dy);
+        cell_plane<D>(C.dv, 0, f, q, w0, e0, e1);
+        float jq = 0.0f;
+        if (D == 3) {
+            float v1, dx1, dy1, w1;
+            cell_plane<D>(C.v, 1, f, q, v1, dx1, dy1);
+            cell_plane<D>(C.dv, 1, f, q, w1, e0, e1);
+            jq = (v1 - v0) * qs[D - 1];
+            v0 = lerp(v0, v1, f[D - 1]);
+            dx = lerp(dx, dx1, f[D - 1]);
+            dy = lerp(dy, dy1, f[D - 1]);
+            w0 = lerp(w0, w1, f[D - 1]);
+        }
+        val[q] = v0;
+        Jq[q] = fmaf(dx, qs[0], fmaf(dy, qs[1], jq));
+        dval[q] = w0;
+    }
+}
+
+template <int D, class SC>
+__device__ __forceinline__ void stage_adjoint_cached(const DevGrid& g, const float* __restrict__ V, SC& S,
+                                                     CellCache<D, false>& C, size_t s0, const int* p, const float* f,
+                                                     const float* mu, float* nu) {
+    const int base = linear<D>(g, p);
+    cache_cell<D, false>(g, V, nullptr, s0, base, C);
+    float c[1 << D];
+#pragma unroll
+    for (int k = 0; k < (1 << D); ++k) {
+        float sk = 0.0f;
+#pragma unroll
+        for (int q = 0; q < D; ++q) sk = fmaf(C.v[k][q], mu[q], sk);
+        c[k] = sk;
+    }
+    const float a0 = lerp(c[0], c[1], f[0]);
+    const float a1 = lerp(c[2], c[3], f[0]);
+    const float s_0 = lerp(a0, a1, f[1]);
+    float dx = lerp(c[1] - c[0], c[3] - c[2], f[1]);
+    float dy = a1 - a0;
+    if (D == 3) {
+        const float b0 = lerp(c[4], c[5], f[0]);
+        const float b1 = lerp(c[6], c[7], f[0]);
+        const float s_1 = lerp(b0, b1, f[1]);
+        const float dx1 = lerp(c[5] - c[4], c[7] - c[6], f[1]);
+        const float dy1 = b1 - b0;
+        nu[D - 1] = (s_1 - s_0) * g.inv_h[D - 1];
+        dx = lerp(dx, dx1, f[D - 1]);
+        dy = lerp(dy, dy1, f[D - 1]);
+    }
+    nu[0] = dx * g.inv_h[0];
+    nu[1] = dy * g.inv_h[1];
+    scatter_add<D>(g, S, s0, base, f, mu);
+}
+
 // T(y) and optionally grad T(y) from the padded image, y at displacement u.
 template <int D, bool GRAD>
 __device__ __forceinline__ float sample_image(const DevGrid& g, const Start<D>& s, const float* __restrict__ Tp,
@@ -624,9 +730,9 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
 
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
-template <int D, bool NS, bool REC>
+template <int D, bool NS, bool REC, bool CACHE>
 __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float* V, const float* dV, float* u,
-                                                 float* dy, int k, float* rec) {
+                                                 float* dy, int k, float* rec, CellCache<D, true>& C) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -640,7 +746,8 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         for (int a = 0; a < D; ++a) rec[a] = u[a];
     }
     locate<D>(A.vg, sv, u, p, f);
-    stage_tangent<D>(A.vg, V, dV, s1, p, f, dy, vs, Jq, dvs);
+    if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s1, p, f, dy, C, vs, Jq, dvs);
+    else stage_tangent<D>(A.vg, V, dV, s1, p, f, dy, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Ds = dvs[a] + Jq[a];
@@ -655,7 +762,8 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         for (int a = 0; a < D; ++a) rec[D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
-    stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
+    if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s2, p, f, q, C, vs, Jq, dvs);
+    else stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Ds = dvs[a] + Jq[a];
@@ -670,7 +778,8 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         for (int a = 0; a < D; ++a) rec[2 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
-    stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
+    if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s2, p, f, q, C, vs, Jq, dvs);
+    else stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Ds = dvs[a] + Jq[a];
@@ -685,7 +794,8 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         for (int a = 0; a < D; ++a) rec[3 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
-    stage_tangent<D>(A.vg, V, dV, s4, p, f, q, vs, Jq, dvs);
+    if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s4, p, f, q, C, vs, Jq, dvs);
+    else stage_tangent<D>(A.vg, V, dV, s4, p, f, q, vs, Jq, dvs);
     const float s6 = dt / 6.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -698,9 +808,9 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
 // scatter the step's contribution into the gradient and return the adjoint of
 // its start.  The stage positions u, u2, u3, u4 were recorded by the forward
 // sweep; each stage's J^T mu and scatter share one pass over its corners.
-template <int D, bool NS, class SC>
+template <int D, bool NS, class SC, bool CACHE>
 __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, SC& S, const float* rec,
-                                                 float* lam, int k) {
+                                                 float* lam, int k, CellCache<D, false>& C) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -714,22 +824,26 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float
 #pragma unroll
     for (int a = 0; a < D; ++a) { mu[a] = c16 * lam[a]; us[a] = rec[3 * D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D, SC>(A.vg, V, S, s4, p, f, mu, nu);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s4, p, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s4, p, f, mu, nu);
     // stage 3: D3 = I(dv, y3) + J3 (dy + dt/2 D2)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); us[a] = rec[2 * D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, p, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 2: D2 = I(dv, y2) + J2 (dy + dt/2 D1)
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); us[a] = rec[D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, p, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
     // stage 1: D1 = I(dv, y) + J1 dy
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); us[a] = rec[a]; }
     locate<D>(A.vg, sv, us, p, f);
-    stage_adjoint<D, SC>(A.vg, V, S, s1, p, f, mu, nu);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s1, p, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s1, p, f, mu, nu);
 #pragma unroll
     for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
 }
@@ -884,12 +998,25 @@ __device__ __forceinline__ double block_sum(double x) {
 // 256 threads; FWD at 64 registers (4 CTAs per SM), the derivative modes at 80
 // (3 CTAs): measured fastest among 64/80/128-register and 256/512-thread
 // configurations on the 128^3 matvec.
+template <int D, int MODEL, int MODE>
+struct TraceOccupancy {
+    // CTAs per SM the register budget is set for: the 3D transport tangent
+    // modes hold two cached cells (v and dv corners) and run at 128 registers
+    // (measured on the 128^3 matvec: 1.42 ms at 3 CTAs without the cache,
+    // 1.50 ms with it at 80 registers, 1.32 ms with it at 128)
+    static constexpr int value =
+        MODE == MODE_FWD ? 4 : ((D == 3 && MODEL == LGNK_TRANSPORT && (MODE == MODE_JVP || MODE == MODE_HESS)) ? 2 : 3);
+};
+
 template <int D, bool NS, int MODEL, int MODE>
-__global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_kernel(const TraceArgs A) {
+__global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::value)) trace_kernel(const TraceArgs A) {
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
     constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD || MODE == MODE_ASM);
     using SC = typename std::conditional<MODE == MODE_ASM, AsmRow<D>, Scatter<D>>::type;
+    // cached velocity cells for transport; the continuity kernels (many time
+    // slices, longer trajectories) were measured faster without
+    constexpr bool CACHE = MODEL == LGNK_TRANSPORT;
     const float* V = static_cast<const float*>(A.V);
     const float* dV = static_cast<const float*>(A.dV);
 
@@ -910,13 +1037,15 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_ke
             u[a] = 0.0f;
             dy[a] = 0.0f;
         }
+        CellCache<D, true> tcache;
+        tcache.key = -1;
         // stage positions of every step (recorded for the adjoint sweep)
         float hist[ADJOINT ? LGNK_MAX_STEPS : 1][4 * D];
 
 #pragma unroll 1
         for (int k = 0; k < A.N; ++k) {
             float* rec = hist[ADJOINT ? k : 0];
-            if (TANGENT) rk4_tangent_step<D, NS, ADJOINT>(A, V, dV, u, dy, k, rec);
+            if (TANGENT) rk4_tangent_step<D, NS, ADJOINT, CACHE>(A, V, dV, u, dy, k, rec, tcache);
             else rk4_step<D, NS, ADJOINT>(A, V, u, k, rec);
         }
         if (A.yout != nullptr) {
@@ -1003,8 +1132,11 @@ __global__ void __launch_bounds__(LGNK_BLOCK, MODE == MODE_FWD ? 4 : 3) trace_ke
         }
 
         if (ADJOINT) {
+            CellCache<D, false> acache;
+            acache.key = -1;
 #pragma unroll 1
-            for (int k = A.N - 1; k >= 0; --k) rk4_adjoint_step<D, NS, SC>(A, V, S, hist[ADJOINT ? k : 0], lam, k);
+            for (int k = A.N - 1; k >= 0; --k)
+                rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, hist[ADJOINT ? k : 0], lam, k, acache);
             scatter_finish<D>(A.vg, S);
             if constexpr (MODE == MODE_ASM) {
                 write_row<D>(A, S, vox);
