@@ -359,6 +359,52 @@ __device__ __forceinline__ void scatter_finish(const DevGrid& g, Scatter<D>& S) 
     if (S.base >= 0) scatter_flush<D>(g, S, false, S.f, S.mu);
 }
 
+// Destination of the adjoint scatter with the whole pending cell in
+// registers: the corner vectors sum_stages w_c(f) mu of consecutive stages in
+// one cell and slice are accumulated and sent as 2^d vector reductions only
+// when the cell or slice changes (the transport matvec, where consecutive
+// stages mostly share a cell).
+template <int D>
+struct BlockScatter {
+    typename VecT<D>::type* G;
+    long long key;            // s0 + base of the pending cell, -1 if none
+    float blk[1 << D][D];
+};
+
+template <int D>
+__device__ __forceinline__ void scatter_init(BlockScatter<D>& S, void* G) {
+    S.G = static_cast<typename VecT<D>::type*>(G);
+    S.key = -1;
+}
+
+template <int D>
+__device__ __forceinline__ void block_flush(const DevGrid& g, BlockScatter<D>& S) {
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c)
+        red_vec(S.G + corner_elem<D>(g, (size_t)S.key, 0, c & 1, (c >> 1) & 1, (c >> 2) & 1), S.blk[c], 1.0f);
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_finish(const DevGrid& g, BlockScatter<D>& S) {
+    if (S.key >= 0) block_flush<D>(g, S);
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_add(const DevGrid& g, BlockScatter<D>& S, size_t s0, int base, const float* f,
+                                            const float* mu) {
+    const long long key = (long long)s0 + base;
+    const bool fresh = key != S.key;
+    if (fresh && S.key >= 0) block_flush<D>(g, S);
+    S.key = key;
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        float w = (c & 1 ? f[0] : 1.0f - f[0]) * ((c >> 1) & 1 ? f[1] : 1.0f - f[1]);
+        if (D == 3) w *= ((c >> 2) & 1) ? f[D - 1] : 1.0f - f[D - 1];
+#pragma unroll
+        for (int q = 0; q < D; ++q) S.blk[c][q] = fresh ? w * mu[q] : fmaf(w, mu[q], S.blk[c][q]);
+    }
+}
+
 // Destination of the adjoint contributions when a row of J is assembled: a
 // per-thread table of (slice, cell) blocks, each the 2^d corner vectors
 // sum_stages w_c(f) mu.  A trajectory stays within a few velocity cells, so a
@@ -370,42 +416,62 @@ struct AsmRow {
     float blk[CAP][(1 << D) * D];
     int n;
     bool overflow;
+    // the block of the current cell, in registers until the cell changes
+    long long pkey;
+    float pblk[(1 << D) * D];
 };
 
 template <int D>
 __device__ __forceinline__ void scatter_init(AsmRow<D>& S, void*) {
     S.n = 0;
     S.overflow = false;
+    S.pkey = -1;
 }
 
+// Add the pending block to the table entry of its cell (a new entry if the
+// row has none yet).
 template <int D>
-__device__ __forceinline__ void scatter_finish(const DevGrid&, AsmRow<D>&) {}
-
-template <int D>
-__device__ __forceinline__ void scatter_add(const DevGrid& g, AsmRow<D>& S, size_t s0, int base, const float* f,
-                                            const float* mu) {
-    (void)g;
-    const long long key = (long long)s0 + base;
+__device__ __forceinline__ void asm_commit(AsmRow<D>& S) {
     int j = S.n - 1;
 #pragma unroll 1
     for (; j >= 0; --j)       // newest first: a trajectory revisits the cell it just left
-        if (S.key[j] == key) break;
+        if (S.key[j] == S.pkey) break;
     if (j < 0) {
         if (S.n == AsmRow<D>::CAP) {
             S.overflow = true;
             return;
         }
         j = S.n++;
-        S.key[j] = key;
+        S.key[j] = S.pkey;
 #pragma unroll
-        for (int k = 0; k < (1 << D) * D; ++k) S.blk[j][k] = 0.0f;
+        for (int k = 0; k < (1 << D) * D; ++k) S.blk[j][k] = S.pblk[k];
+        return;
     }
+#pragma unroll
+    for (int k = 0; k < (1 << D) * D; ++k) S.blk[j][k] += S.pblk[k];
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_finish(const DevGrid&, AsmRow<D>& S) {
+    if (S.pkey >= 0) asm_commit<D>(S);
+    S.pkey = -1;
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_add(const DevGrid& g, AsmRow<D>& S, size_t s0, int base, const float* f,
+                                            const float* mu) {
+    (void)g;
+    const long long key = (long long)s0 + base;
+    const bool fresh = key != S.pkey;
+    if (fresh && S.pkey >= 0) asm_commit<D>(S);
+    S.pkey = key;
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
         float w = (c & 1 ? f[0] : 1.0f - f[0]) * ((c >> 1) & 1 ? f[1] : 1.0f - f[1]);
         if (D == 3) w *= ((c >> 2) & 1) ? f[D - 1] : 1.0f - f[D - 1];
 #pragma unroll
-        for (int q = 0; q < D; ++q) S.blk[j][c * D + q] = fmaf(w, mu[q], S.blk[j][c * D + q]);
+        for (int q = 0; q < D; ++q)
+            S.pblk[c * D + q] = fresh ? w * mu[q] : fmaf(w, mu[q], S.pblk[c * D + q]);
     }
 }
 
@@ -1000,12 +1066,13 @@ __device__ __forceinline__ double block_sum(double x) {
 // configurations on the 128^3 matvec.
 template <int D, int MODEL, int MODE>
 struct TraceOccupancy {
-    // CTAs per SM the register budget is set for: the 3D transport tangent
-    // modes hold two cached cells (v and dv corners) and run at 128 registers
-    // (measured on the 128^3 matvec: 1.42 ms at 3 CTAs without the cache,
-    // 1.50 ms with it at 80 registers, 1.32 ms with it at 128)
+    // CTAs per SM the register budget is set for: the 3D transport modes hold
+    // cached cells (v and dv corners) and the pending scatter block and run at
+    // 128 registers (measured on the 128^3 matvec: 1.42 ms at 3 CTAs without
+    // either, 1.50 ms with the cache at 80 registers, 1.31 ms with it at 128,
+    // 0.82 ms with the scatter block as well)
     static constexpr int value =
-        MODE == MODE_FWD ? 4 : ((D == 3 && MODEL == LGNK_TRANSPORT && (MODE == MODE_JVP || MODE == MODE_HESS)) ? 2 : 3);
+        MODE == MODE_FWD ? 4 : ((D == 3 && MODEL == LGNK_TRANSPORT && MODE != MODE_ASM) ? 2 : 3);
 };
 
 template <int D, bool NS, int MODEL, int MODE>
@@ -1013,9 +1080,12 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
     constexpr bool ADJOINT = (MODE == MODE_JTVP || MODE == MODE_HESS || MODE == MODE_OBJGRAD || MODE == MODE_ASM);
-    using SC = typename std::conditional<MODE == MODE_ASM, AsmRow<D>, Scatter<D>>::type;
-    // cached velocity cells for transport; the continuity kernels (many time
-    // slices, longer trajectories) were measured faster without
+    using SC = typename std::conditional<
+        MODE == MODE_ASM, AsmRow<D>,
+        typename std::conditional<(MODE == MODE_HESS || MODE == MODE_JTVP || MODE == MODE_OBJGRAD) && MODEL == LGNK_TRANSPORT, BlockScatter<D>, Scatter<D>>::type>::type;
+    // cached velocity cells and whole-cell scatter blocks for transport; the
+    // continuity kernels (many time slices, longer trajectories) were measured
+    // faster without either
     constexpr bool CACHE = MODEL == LGNK_TRANSPORT;
     const float* V = static_cast<const float*>(A.V);
     const float* dV = static_cast<const float*>(A.dV);
