@@ -410,21 +410,28 @@ __device__ __forceinline__ void scatter_add(const DevGrid& g, BlockScatter<D>& S
 // sum_stages w_c(f) mu.  A trajectory stays within a few velocity cells, so a
 // row has few blocks; a row that needs more than CAP sets `overflow`.
 template <int D>
-struct AsmRow {
+struct AsmTable {
     static constexpr int CAP = D == 3 ? 16 : 32;
     long long key[CAP];
     float blk[CAP][(1 << D) * D];
     int n;
     bool overflow;
-    // the block of the current cell, in registers until the cell changes
+};
+
+// The table is indexed by entry and lives in local memory; the block of the
+// current cell is a separate object, indexed statically, so that it stays in
+// registers until the cell changes (kept in the table's struct it was placed
+// in local memory with it: 1.23 ms for the 128^3 assembly, 0.79 ms apart).
+template <int D>
+struct AsmRow {
+    static constexpr int CAP = AsmTable<D>::CAP;
+    AsmTable<D>* tab;
     long long pkey;
     float pblk[(1 << D) * D];
 };
 
 template <int D>
 __device__ __forceinline__ void scatter_init(AsmRow<D>& S, void*) {
-    S.n = 0;
-    S.overflow = false;
     S.pkey = -1;
 }
 
@@ -432,23 +439,24 @@ __device__ __forceinline__ void scatter_init(AsmRow<D>& S, void*) {
 // row has none yet).
 template <int D>
 __device__ __forceinline__ void asm_commit(AsmRow<D>& S) {
-    int j = S.n - 1;
+    AsmTable<D>& T = *S.tab;
+    int j = T.n - 1;
 #pragma unroll 1
     for (; j >= 0; --j)       // newest first: a trajectory revisits the cell it just left
-        if (S.key[j] == S.pkey) break;
+        if (T.key[j] == S.pkey) break;
     if (j < 0) {
-        if (S.n == AsmRow<D>::CAP) {
-            S.overflow = true;
+        if (T.n == AsmTable<D>::CAP) {
+            T.overflow = true;
             return;
         }
-        j = S.n++;
-        S.key[j] = S.pkey;
+        j = T.n++;
+        T.key[j] = S.pkey;
 #pragma unroll
-        for (int k = 0; k < (1 << D) * D; ++k) S.blk[j][k] = S.pblk[k];
+        for (int k = 0; k < (1 << D) * D; ++k) T.blk[j][k] = S.pblk[k];
         return;
     }
 #pragma unroll
-    for (int k = 0; k < (1 << D) * D; ++k) S.blk[j][k] += S.pblk[k];
+    for (int k = 0; k < (1 << D) * D; ++k) T.blk[j][k] += S.pblk[k];
 }
 
 template <int D>
@@ -918,7 +926,7 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float
 // [e][i], its block of 2^d corner vectors contiguous at [e][i][corner][q]
 // (96 bytes in 3D, 32 in 2D), so a warp streams one contiguous range per entry.
 template <int D>
-__device__ __forceinline__ void write_row(const TraceArgs& A, const AsmRow<D>& S, int vox) {
+__device__ __forceinline__ void write_row(const TraceArgs& A, const AsmTable<D>& S, int vox) {
     const long long M = (long long)A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
     if (S.overflow || S.n > A.ewidth) {
         A.ecnt[vox] = 0;
@@ -1070,9 +1078,10 @@ struct TraceOccupancy {
     // cached cells (v and dv corners) and the pending scatter block and run at
     // 128 registers (measured on the 128^3 matvec: 1.42 ms at 3 CTAs without
     // either, 1.50 ms with the cache at 80 registers, 1.31 ms with it at 128,
-    // 0.82 ms with the scatter block as well)
+    // 0.82 ms with the scatter block as well; the assembly 1.23 -> 0.79 ms
+    // from 3 to 2 CTAs with its pending block in registers)
     static constexpr int value =
-        MODE == MODE_FWD ? 4 : ((D == 3 && MODEL == LGNK_TRANSPORT && MODE != MODE_ASM) ? 2 : 3);
+        MODE == MODE_FWD ? 4 : ((D == 3 && MODEL == LGNK_TRANSPORT) ? 2 : 3);
 };
 
 template <int D, bool NS, int MODEL, int MODE>
@@ -1098,6 +1107,12 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
 
     SC S;
     scatter_init<D>(S, A.G);
+    AsmTable<D> row_table;        // MODE_ASM: the row being assembled
+    if constexpr (MODE == MODE_ASM) {
+        row_table.n = 0;
+        row_table.overflow = false;
+        S.tab = &row_table;
+    }
 
     if (active) {
         const int vox = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
@@ -1209,8 +1224,8 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
                 rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, hist[ADJOINT ? k : 0], lam, k, acache);
             scatter_finish<D>(A.vg, S);
             if constexpr (MODE == MODE_ASM) {
-                write_row<D>(A, S, vox);
-                entries = (double)S.n;
+                write_row<D>(A, *S.tab, vox);
+                entries = (double)S.tab->n;
             }
         }
     }
