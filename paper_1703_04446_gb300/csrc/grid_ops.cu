@@ -4,6 +4,8 @@
 // preconditioner (Sec. 3.2) and the vector updates of PCG.
 #include <cmath>
 
+#include <algorithm>
+
 #include "lgnk_internal.h"
 
 namespace {
@@ -358,81 +360,117 @@ __global__ void dct_axis_kernel(const float* __restrict__ in, float* __restrict_
     }
 }
 
-// The same transform for axes of at most kDctTileMax cells, staged in shared
-// memory.  Each array block is viewed as [outer][m][inner] (inner = product
-// of the cell counts of the axes below `axis`).  A CTA transforms 32 lines:
-// 32 consecutive inner positions of one outer index (axis > 0), or 32
-// consecutive x rows (axis 0, inner = 1; the tile is transposed through
-// shared memory so that loads and stores stay coalesced).  The m x m matrix
-// (transposed for the inverse) sits in shared memory; warp w computes the
-// outputs k = w, w + 8, ... of all 32 lines, reading the matrix entry as a
-// broadcast and the tile without bank conflicts.
+// The same transform for axes of at most kDctTileMax cells, as a small
+// register-blocked matrix product staged in shared memory.  Each array block
+// is viewed as [outer][m][inner] (inner = product of the cell counts of the
+// axes below `axis`).  A CTA transforms 64 lines: 64 consecutive inner
+// positions of one outer index (axis > 0), or 64 consecutive x rows (axis 0,
+// inner = 1; loaded and stored through shared memory so that global accesses
+// stay coalesced).  The coefficient matrix sits in shared memory transposed,
+// [q][k], and the tile as [q][line]; a thread computes a 4 x 4 block of
+// (output index k, line), reading one float4 of each per q for 16 FMAs.  Every
+// output is accumulated over q in increasing order, as in dct_axis_kernel.
 constexpr int kDctTileMax = 128;
-constexpr int kDctLines = 32;
-constexpr int kDctRowsPerWarp = kDctTileMax / (kBlock / 32);
+constexpr int kDctLines = 64;
+constexpr int kDctLS = kDctLines + 4;        // tile row stride (float4-aligned)
 
 template <bool XAXIS>
 __global__ void __launch_bounds__(kBlock) dct_tile_kernel(const float* __restrict__ in, float* __restrict__ out,
                                                           const float* __restrict__ C, int m, long long inner,
                                                           long long lines, int inverse) {
-    extern __shared__ float sm[];
-    float* Cs = sm;                   // [k][q]
-    float* tile = sm + m * m;         // [q][l], row stride kDctLines + 1
-    constexpr int TS = kDctLines + 1;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int e = t; e < m * m; e += kBlock) {
-        const int k = e / m, q = e % m;
-        Cs[e] = inverse ? __ldg(C + (size_t)q * m + k) : __ldg(C + e);
+    extern __shared__ __align__(16) float sm[];
+    const int MP = (m + 3) & ~3;                 // k padded to whole float4s
+    float* Ct = sm;                              // [q][MP]
+    float* tile = sm + m * MP;                   // [q][kDctLS], later the output stage of axis 0
+    const int t = threadIdx.x;
+    for (int e = t; e < m * MP; e += kBlock) {
+        const int q = e / MP, k = e % MP;
+        float c = 0.0f;
+        if (k < m) c = inverse ? __ldg(C + (size_t)q * m + k) : __ldg(C + (size_t)k * m + q);
+        Ct[e] = c;
     }
     long long o = 0, i0 = 0, r0 = 0;
     if (XAXIS) {
         r0 = (long long)blockIdx.x * kDctLines;
         for (int e = t; e < kDctLines * m; e += kBlock) {
             const int l = e / m, q = e % m;
-            tile[q * TS + l] = (r0 + l < lines) ? __ldg(in + (size_t)(r0 + l) * m + q) : 0.0f;
+            tile[q * kDctLS + l] = (r0 + l < lines) ? __ldg(in + (size_t)(r0 + l) * m + q) : 0.0f;
         }
     } else {
         o = blockIdx.y;
         i0 = (long long)blockIdx.x * kDctLines;
         for (int e = t; e < kDctLines * m; e += kBlock) {
             const int q = e / kDctLines, l = e % kDctLines;
-            tile[q * TS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
+            tile[q * kDctLS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
         }
     }
     __syncthreads();
-    float acc[kDctRowsPerWarp];
+    const int ntask = (MP / 4) * (kDctLines / 4);
+    constexpr int SS = kDctTileMax + 1;          // output stage row stride (axis 0)
+    float acc[2][4][4];                          // at most two tasks per thread (MP <= 128)
 #pragma unroll
-    for (int j = 0; j < kDctRowsPerWarp; ++j) acc[j] = 0.0f;
+    for (int r = 0; r < 2; ++r) {
+        const int task = t + r * kBlock;
+        if (task >= ntask) break;
+        const int kb = task / (kDctLines / 4), lb = task % (kDctLines / 4);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[r][i][j] = 0.0f;
+        const float4* cp = reinterpret_cast<const float4*>(Ct) + kb;
+        const float4* xp = reinterpret_cast<const float4*>(tile) + lb;
 #pragma unroll 4
-    for (int q = 0; q < m; ++q) {
-        const float x = tile[q * TS + lane];
+        for (int q = 0; q < m; ++q) {
+            const float4 c = cp[q * (MP / 4)];
+            const float4 x = xp[q * (kDctLS / 4)];
+            const float cv[4] = {c.x, c.y, c.z, c.w}, xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-        for (int j = 0; j < kDctRowsPerWarp; ++j) {
-            const int k = warp + 8 * j;
-            if (k < m) acc[j] = fmaf(Cs[k * m + q], x, acc[j]);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[r][i][j] = fmaf(cv[i], xv[j], acc[r][i][j]);
+        }
+        if (!XAXIS) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * kb + i;
+                if (k >= m) break;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long long l = i0 + 4 * lb + j;
+                    if (l < inner) out[((size_t)o * m + k) * inner + l] = acc[r][i][j];
+                }
+            }
         }
     }
     if (XAXIS) {
-        __syncthreads();              // the tile becomes the output stage [l][k]
+        __syncthreads();                         // the tile becomes the output stage [line][k]
         float* stage = tile;
-        const int OS = m + 1;
 #pragma unroll
-        for (int j = 0; j < kDctRowsPerWarp; ++j) {
-            const int k = warp + 8 * j;
-            if (k < m) stage[lane * OS + k] = acc[j];
+        for (int r = 0; r < 2; ++r) {
+            const int task = t + r * kBlock;
+            if (task >= ntask) break;
+            const int kb = task / (kDctLines / 4), lb = task % (kDctLines / 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * kb + i;
+                if (k >= m) break;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) stage[(4 * lb + j) * SS + k] = acc[r][i][j];
+            }
         }
         __syncthreads();
         for (int e = t; e < kDctLines * m; e += kBlock) {
             const int l = e / m, k = e % m;
-            if (r0 + l < lines) out[(size_t)(r0 + l) * m + k] = stage[l * OS + k];
-        }
-    } else if (i0 + lane < inner) {
-#pragma unroll
-        for (int j = 0; j < kDctRowsPerWarp; ++j) {
-            const int k = warp + 8 * j;
-            if (k < m) out[((size_t)o * m + k) * inner + i0 + lane] = acc[j];
+            if (r0 + l < lines) out[(size_t)(r0 + l) * m + k] = stage[l * SS + k];
         }
     }
+}
+
+// Shared memory of dct_tile_kernel for an axis of m cells (bytes).
+inline size_t dct_tile_smem(int m) {
+    const size_t MP = (size_t)((m + 3) & ~3);
+    const size_t tile = std::max((size_t)m * kDctLS, (size_t)kDctLines * (kDctTileMax + 1));
+    return ((size_t)m * MP + tile) * sizeof(float);
 }
 
 __global__ void scale_modes_kernel(float* x, const float* __restrict__ inv_eig, size_t block_elems, size_t count) {
@@ -736,22 +774,19 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const D
         dct_axis_kernel<<<grid_for(total), kBlock, 0, s>>>(in, out, C, g, nblocks_kd, axis, inverse ? 1 : 0);
         return cudaGetLastError();
     }
-    // stage: the matrix plus a 32-line tile (also the transposed output stage of axis 0)
-    const size_t smem = ((size_t)m * m + (size_t)m * (kDctLines + 1) + kDctLines) * sizeof(float);
+    const size_t smem = dct_tile_smem(m);
     // the dynamic shared-memory limit is raised once per device and kernel
     static bool attr_set_dev[64][2] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     bool* attr_set = attr_set_dev[dev];
+    const int smem_max = (int)dct_tile_smem(kDctTileMax);
     const long long inner = axis == 0 ? 1 : (axis == 1 ? (long long)g.m[0] : (long long)g.m[0] * g.m[1]);
     const long long outer = (long long)(total / ((size_t)m * inner));
     if (axis == 0) {
         if (!attr_set[0]) {
-            const cudaError_t e = cudaFuncSetAttribute(dct_tile_kernel<true>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)(((size_t)kDctTileMax * kDctTileMax +
-                                                              (size_t)kDctTileMax * (kDctLines + 1) + kDctLines) *
-                                                             sizeof(float)));
+            const cudaError_t e =
+                cudaFuncSetAttribute(dct_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
             if (e != cudaSuccess) return e;
             attr_set[0] = true;
         }
@@ -760,11 +795,8 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const D
             in, out, C, m, 1, rows, inverse ? 1 : 0);
     } else {
         if (!attr_set[1]) {
-            const cudaError_t e = cudaFuncSetAttribute(dct_tile_kernel<false>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)(((size_t)kDctTileMax * kDctTileMax +
-                                                              (size_t)kDctTileMax * (kDctLines + 1) + kDctLines) *
-                                                             sizeof(float)));
+            const cudaError_t e =
+                cudaFuncSetAttribute(dct_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
             if (e != cudaSuccess) return e;
             attr_set[1] = true;
         }
