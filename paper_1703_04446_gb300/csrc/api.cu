@@ -50,6 +50,7 @@ struct lgnk_ctx {
     double* dres = nullptr;
     double* hres = nullptr;       // pinned host mirror of dres
     float* fsc = nullptr;         // PCG step lengths on the device (alpha, -alpha, beta)
+    unsigned* dcounter = nullptr; // completion counter of launch_dot_fused (zero between launches)
     // lgnk_solve runs on a stream of its own (capturable, unlike the legacy
     // default stream), ordered after and before the caller's stream by events
     cudaStream_t solve_stream = nullptr;
@@ -689,6 +690,11 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     if ((s = dalloc(ctx, (size_t)ctx->trace_blocks, &ctx->cpartial)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 8, &ctx->dres)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 4, &ctx->fsc)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, 1, &ctx->dcounter)) != LGNK_OK) return fail(s);
+    if (cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LGNK_ERR_CUDA);
+    }
     if (cudaMallocHost((void**)&ctx->hres, 8 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         ctx->hres = nullptr;
@@ -1002,16 +1008,12 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
         // the device work of one iteration; ends with p.Hp and r.r in hres[2], hres[3]
         auto body = [&]() -> lgnk_status {
             TRY(use_asm ? hessvec_assembled_packed(ctx, p, Hp) : hessvec_packed(ctx, T, p, Hp));
-            TRY(dot_dev(ctx, p, Hp, n, 2));
-            KL(launch_pcg_scalars(ctx->dres, ctx->fsc, 0, s));
+            KL(launch_dot_fused(p, Hp, nullptr, n, ctx->partial, nb, ctx->dcounter, ctx->dres, 2, 2, 0, ctx->fsc, s));
             KL(launch_axpby_dev(0.0f, ctx->fsc + 0, p, 1.0f, nullptr, x, n, s));
             KL(launch_axpby_dev(0.0f, ctx->fsc + 1, Hp, 1.0f, nullptr, r, n, s));
             if (o.precond) TRY(precond_apply(ctx, r, z));
             else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-            KL(launch_dot2(r, r, z, n, ctx->partial, nb, s));
-            KL(launch_reduce(ctx->partial, nb, ctx->dres + 3, s));
-            KL(launch_reduce(ctx->partial + nb, nb, ctx->dres + 4, s));
-            KL(launch_pcg_scalars(ctx->dres, ctx->fsc, 1, s));
+            KL(launch_dot_fused(r, r, z, n, ctx->partial, nb, ctx->dcounter, ctx->dres, 3, 4, 1, ctx->fsc, s));
             KL(launch_axpby_dev(1.0f, nullptr, z, 0.0f, ctx->fsc + 2, p, n, s));
             CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
             return LGNK_OK;

@@ -183,39 +183,65 @@ __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// Two inner products sharing the first operand in one pass: partial[b] =
-// sum a.b and partial[nblocks + b] = sum a.c over block b's slice.
-__global__ void dot2_kernel(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ c,
-                            size_t count, double* partial) {
-    double s = 0.0, t = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const double ai = (double)a[i];
-        s += ai * (double)b[i];
-        t += ai * (double)c[i];
-    }
-    s = block_reduce(s);
-    __syncthreads();          // block_reduce's shared slots are reused
-    t = block_reduce(t);
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = s;
-        partial[gridDim.x + blockIdx.x] = t;
-    }
-}
-
-// PCG step lengths kept on the device (Eq. 11 solve): sc holds the FP64 inner
-// products [2] p.Hp, [3] r.r, [4] r.z (new), [5] r.z (current).
+// One or two inner products sharing the first operand, finished in the same
+// launch: every block writes its FP64 partial sums, and the last block to
+// finish (a counter, reset by that block) adds the partials in block order
+// (deterministic) into sc[slot_b] (a.b) and sc[slot_c] (a.c, when c is
+// given), then the PCG step lengths of step `mode` (-1: none) from the FP64
+// inner products in sc ([2] p.Hp, [3] r.r, [4] r.z new, [5] r.z current):
 //   mode 0: alpha = rz / pHp, or 0 when pHp is not positive; f[0] = alpha, f[1] = -alpha
 //   mode 1: beta = rz_new / rz, then rz = rz_new;             f[2] = beta
-__global__ void pcg_scalars_kernel(double* sc, float* f, int mode) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void pcg_step_lengths(double* sc, float* f, int mode) {
     if (mode == 0) {
         const double php = sc[2];
         const double a = php > 0.0 ? sc[5] / php : 0.0;
         f[0] = (float)a;
         f[1] = (float)-a;
-    } else {
+    } else if (mode == 1) {
         f[2] = (float)(sc[4] / sc[5]);
         sc[5] = sc[4];
+    }
+}
+
+__global__ void dot_fused_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                 const float* __restrict__ c, size_t count, double* partial, unsigned* counter,
+                                 double* sc, int slot_b, int slot_c, int mode, float* f) {
+    double s = 0.0, t = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const double ai = (double)a[i];
+        s += ai * (double)b[i];
+        if (c != nullptr) t += ai * (double)c[i];
+    }
+    s = block_reduce(s);
+    if (c != nullptr) {
+        __syncthreads();      // block_reduce's shared slots are reused
+        t = block_reduce(t);
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s;
+        if (c != nullptr) partial[gridDim.x + blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double u = 0.0, w = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        u += ((volatile double*)partial)[i];
+        if (c != nullptr) w += ((volatile double*)partial)[gridDim.x + i];
+    }
+    u = block_reduce(u);
+    if (c != nullptr) {
+        __syncthreads();
+        w = block_reduce(w);
+    }
+    if (threadIdx.x == 0) {
+        sc[slot_b] = u;
+        if (c != nullptr) sc[slot_c] = w;
+        pcg_step_lengths(sc, f, mode);
+        *counter = 0u;
     }
 }
 
@@ -711,14 +737,10 @@ int dot_blocks(size_t count) {
     return b < kReduceBlocks ? (b > 0 ? b : 1) : kReduceBlocks;
 }
 
-cudaError_t launch_dot2(const float* a, const float* b, const float* c, size_t count, double* partial, int nblocks,
-                        cudaStream_t s) {
-    dot2_kernel<<<nblocks, kBlock, 0, s>>>(a, b, c, count, partial);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pcg_scalars(double* sc, float* f, int mode, cudaStream_t s) {
-    pcg_scalars_kernel<<<1, 32, 0, s>>>(sc, f, mode);
+cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, size_t count, double* partial,
+                             int nblocks, unsigned* counter, double* sc, int slot_b, int slot_c, int mode, float* f,
+                             cudaStream_t s) {
+    dot_fused_kernel<<<nblocks, kBlock, 0, s>>>(a, b, c, count, partial, counter, sc, slot_b, slot_c, mode, f);
     return cudaGetLastError();
 }
 

@@ -119,11 +119,11 @@ cudaError_t launch_reduce(const double* partial, int count, double* out, cudaStr
 cudaError_t launch_dot(const float* a, const float* b, size_t count, double* partial, int nblocks,
                        cudaStream_t s);
 int dot_blocks(size_t count);
-// partial[0..nblocks) = a.b, partial[nblocks..2 nblocks) = a.c (per-block FP64 sums)
-cudaError_t launch_dot2(const float* a, const float* b, const float* c, size_t count, double* partial, int nblocks,
-                        cudaStream_t s);
-// PCG step lengths from device inner products (see grid_ops.cu)
-cudaError_t launch_pcg_scalars(double* sc, float* f, int mode, cudaStream_t s);
+// a.b (and a.c) reduced to sc[slot_b] (sc[slot_c]) in one launch, then the PCG
+// step `mode` (-1 none, 0 alpha, 1 beta); counter: a zeroed device word
+cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, size_t count, double* partial,
+                             int nblocks, unsigned* counter, double* sc, int slot_b, int slot_c, int mode, float* f,
+                             cudaStream_t s);
 cudaError_t launch_axpby_dev(float a, const float* ap, const float* x, float b, const float* bp, float* y,
                              size_t count, cudaStream_t s);
 // out = addsrc + scale * A x + gamma * x for the Neumann Laplacian A = B^T B of each
