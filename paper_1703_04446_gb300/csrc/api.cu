@@ -51,6 +51,8 @@ struct lgnk_ctx {
     double* hres = nullptr;       // pinned host mirror of dres
     float* fsc = nullptr;         // PCG step lengths on the device (alpha, -alpha, beta)
     unsigned* dcounter = nullptr; // completion counter of launch_dot_fused (zero between launches)
+    int* dctl = nullptr;          // device-side PCG loop state (launch_pcg_control)
+    unsigned char* hpin = nullptr; // pinned: the loop state's host copy (4 ints) and its tolerance (a double)
     // lgnk_solve runs on a stream of its own (capturable, unlike the legacy
     // default stream), ordered after and before the caller's stream by events
     cudaStream_t solve_stream = nullptr;
@@ -606,6 +608,7 @@ void lgnk_destroy(lgnk_ctx* ctx) {
     if (ctx->solve_stream) cudaStreamDestroy(ctx->solve_stream);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->hres) cudaFreeHost(ctx->hres);
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
     delete ctx;
 }
 
@@ -691,6 +694,12 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     if ((s = dalloc(ctx, 8, &ctx->dres)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 4, &ctx->fsc)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 1, &ctx->dcounter)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, 4, &ctx->dctl)) != LGNK_OK) return fail(s);
+    if (cudaMallocHost((void**)&ctx->hpin, 64) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->hpin = nullptr;
+        return fail(LGNK_ERR_OOM);
+    }
     if (cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(LGNK_ERR_CUDA);
@@ -938,6 +947,21 @@ struct PcgGraph {
     }
 };
 
+// The whole PCG loop of one GN step as one graph: a while node whose body is
+// one iteration followed by launch_pcg_control, which ends the loop on the
+// stopping test, non-positive curvature or the iteration cap.  The host reads
+// the loop state once per GN step instead of once per iteration.
+struct PcgLoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0, trace_launches = 0;   // per iteration
+    bool failed = false;
+    ~PcgLoopGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
 lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts& o,
                        lgnk_solve_report* rep_out) {
     const auto t_start = std::chrono::steady_clock::now();
@@ -950,6 +974,7 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
     const size_t n = ctx->n;
     cudaStream_t s = ctx->stream;
     PcgGraph graphs[2];           // [0] matrix-free, [1] assembled
+    PcgLoopGraph loops[2];
     lgnk_solve_report rep;
     memset(&rep, 0, sizeof(rep));
 
@@ -1006,7 +1031,7 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
         // CUDA graphs need a capturable stream and no per-launch profiling events
         const bool use_graphs = !ctx->prof && s == ctx->solve_stream && s != nullptr;
         // the device work of one iteration; ends with p.Hp and r.r in hres[2], hres[3]
-        auto body = [&]() -> lgnk_status {
+        auto body = [&](bool readback) -> lgnk_status {
             TRY(use_asm ? hessvec_assembled_packed(ctx, p, Hp) : hessvec_packed(ctx, T, p, Hp));
             KL(launch_dot_fused(p, Hp, nullptr, n, ctx->partial, nb, ctx->dcounter, ctx->dres, 2, 2, 0, ctx->fsc, s));
             KL(launch_axpby_dev(0.0f, ctx->fsc + 0, p, 1.0f, nullptr, x, n, s));
@@ -1015,19 +1040,82 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
             KL(launch_dot_fused(r, r, z, n, ctx->partial, nb, ctx->dcounter, ctx->dres, 3, 4, 1, ctx->fsc, s));
             KL(launch_axpby_dev(1.0f, nullptr, z, 0.0f, ctx->fsc + 2, p, n, s));
-            CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            if (readback) CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
             return LGNK_OK;
         };
         PcgGraph& gr = graphs[use_asm ? 1 : 0];
+        PcgLoopGraph& lg = loops[use_asm ? 1 : 0];
         int pit = 0;
-        for (int i = 1; i <= o.max_pcg; ++i) {
+        if (use_graphs && lg.exec == nullptr && !lg.failed) {
+            // build the loop graph; any failure falls back to one graph per iteration
+            const long long l0 = ctx->launches, t0 = ctx->trace_launches;
+            cudaGraphConditionalHandle handle = 0;
+            bool ok = cudaGraphCreate(&lg.graph, 0) == cudaSuccess;
+            ok = ok && cudaGraphConditionalHandleCreate(&handle, lg.graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+            cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};   // the rest zero
+            np.conditional.handle = handle;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            ok = ok && cudaGraphAddNode(&node, lg.graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+            if (ok) {
+                ok = cudaStreamBeginCaptureToGraph(s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    bool bok = body(false) == LGNK_OK;
+                    if (bok) {
+                        ctx->launches++;
+                        bok = launch_pcg_control(ctx->dres, ctx->dctl, handle, s) == cudaSuccess;
+                    }
+                    cudaGraph_t captured = nullptr;
+                    ok = (cudaStreamEndCapture(s, &captured) == cudaSuccess) && bok;
+                }
+            }
+            ok = ok && cudaGraphInstantiate(&lg.exec, lg.graph, 0) == cudaSuccess;
+            cudaGetLastError();
+            lg.launches = ctx->launches - l0;
+            lg.trace_launches = ctx->trace_launches - t0;
+            ctx->launches = l0;
+            ctx->trace_launches = t0;
+            if (!ok) {
+                if (lg.exec) cudaGraphExecDestroy(lg.exec);
+                lg.exec = nullptr;
+                lg.failed = true;
+                ctx->err[0] = 0;
+            }
+        }
+        if (lg.exec != nullptr) {
+            int* hc = reinterpret_cast<int*>(ctx->hpin);
+            double* htol = reinterpret_cast<double*>(ctx->hpin + 32);
+            hc[0] = 0;
+            hc[1] = 0;
+            hc[2] = 0;
+            hc[3] = o.max_pcg;
+            *htol = o.pcg_rtol * gn;
+            CK(cudaMemcpyAsync(ctx->dctl, hc, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(ctx->dres + 6, htol, sizeof(double), cudaMemcpyHostToDevice, s));
+            CK(cudaGraphLaunch(lg.exec, s));
+            CK(cudaMemcpyAsync(hc, ctx->dctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int its = hc[0];
+            rep.hessvecs += its;
+            ctx->launches += its * lg.launches;
+            ctx->trace_launches += its * lg.trace_launches;
+            if (hc[2] == 2) {
+                SETERR("non-finite inner product in PCG");
+                return LGNK_ERR_NUMERIC;
+            }
+            pit = hc[1];
+            if (hc[2] == 1 && pit == 0) CK(cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
+        for (int i = 1; lg.exec == nullptr && i <= o.max_pcg; ++i) {
             if (use_graphs && gr.exec == nullptr && !gr.failed) {
                 // capture; any failure ends the capture and falls back to direct launches
                 const long long l0 = ctx->launches, t0 = ctx->trace_launches;
                 cudaGraph_t graph = nullptr;
                 bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
                 if (ok) {
-                    ok = body() == LGNK_OK;
+                    ok = body(true) == LGNK_OK;
                     ok = (cudaStreamEndCapture(s, &graph) == cudaSuccess) && ok && graph != nullptr;
                 }
                 if (ok) ok = cudaGraphInstantiate(&gr.exec, graph, 0) == cudaSuccess;
@@ -1049,7 +1137,7 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
                 ctx->launches += gr.launches;
                 ctx->trace_launches += gr.trace_launches;
             } else {
-                TRY(body());
+                TRY(body(true));
             }
             CK(cudaStreamSynchronize(s));
             rep.hessvecs++;

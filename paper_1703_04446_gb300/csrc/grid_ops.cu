@@ -245,6 +245,28 @@ __global__ void dot_fused_kernel(const float* __restrict__ a, const float* __res
     }
 }
 
+// End of one PCG iteration inside a device-side loop (a CUDA-graph while
+// node): the same tests the host loop makes, on sc[2] = p.Hp, sc[3] = r.r and
+// the tolerance sc[6] = pcg_rtol |g|.  ctl: [0] iterations run, [1] accepted
+// iterations, [2] 1 = non-positive curvature, 2 = non-finite, [3] the cap.
+// The loop continues while the handle is non-zero; the cap ends it.
+__global__ void pcg_control_kernel(const double* sc, int* ctl, cudaGraphConditionalHandle handle) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int it = ctl[0] + 1;
+    ctl[0] = it;
+    const double php = sc[2], rr = sc[3];
+    unsigned go = 0;
+    if (!isfinite(php) || !isfinite(rr)) {
+        ctl[2] = 2;
+    } else if (!(php > 0.0)) {
+        ctl[2] = 1;
+    } else {
+        ctl[1] = it;
+        go = (sqrt(rr) <= sc[6] || it >= ctl[3]) ? 0u : 1u;
+    }
+    cudaGraphSetConditional(handle, go);
+}
+
 // y = a x + b y, a = *ap when ap is given, b = *bp when bp is given.
 __global__ void axpby_dev_kernel(float a, const float* __restrict__ ap, const float* __restrict__ x, float b,
                                  const float* __restrict__ bp, float* y, size_t count) {
@@ -741,6 +763,11 @@ cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, siz
                              int nblocks, unsigned* counter, double* sc, int slot_b, int slot_c, int mode, float* f,
                              cudaStream_t s) {
     dot_fused_kernel<<<nblocks, kBlock, 0, s>>>(a, b, c, count, partial, counter, sc, slot_b, slot_c, mode, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_control(const double* sc, int* ctl, cudaGraphConditionalHandle handle, cudaStream_t s) {
+    pcg_control_kernel<<<1, 32, 0, s>>>(sc, ctl, handle);
     return cudaGetLastError();
 }
 

@@ -124,6 +124,8 @@ int dot_blocks(size_t count);
 cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, size_t count, double* partial,
                              int nblocks, unsigned* counter, double* sc, int slot_b, int slot_c, int mode, float* f,
                              cudaStream_t s);
+// PCG loop test at the end of an iteration of a device-side while loop (see grid_ops.cu)
+cudaError_t launch_pcg_control(const double* sc, int* ctl, cudaGraphConditionalHandle handle, cudaStream_t s);
 cudaError_t launch_axpby_dev(float a, const float* ap, const float* x, float b, const float* bp, float* y,
                              size_t count, cudaStream_t s);
 // out = addsrc + scale * A x + gamma * x for the Neumann Laplacian A = B^T B of each
