@@ -13,6 +13,7 @@ import torch
 from oracle import lagrangian as L
 from oracle.objective import gradient, hessvec, objective, reg_operator
 from oracle.solver import apply_preconditioner
+from paper_1703_04446_gb300 import synth
 from tests._cases import CASES, make_case, rel
 
 pytestmark = pytest.mark.gpu
@@ -184,6 +185,39 @@ def test_max_steps_and_degenerate_axis():
                                       op2.igrid, 3)[0]) <= TOL
     H2 = ctx2.hessvec(torch.from_numpy(v).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(dv).cuda())
     assert rel(_np(H2), hessvec(op2, v.astype(np.float64), T.astype(np.float64), dv.astype(np.float64))) <= TOL
+
+
+@pytest.mark.parametrize("model", ["transport", "continuity"])
+def test_max_steps_3d_time_dependent(model):
+    """N = 64 (the largest the kernels record) with three time nodes (129 time
+    slices) on a ragged 3D grid: the longest stage record and the most slices."""
+    from paper_1703_04446_gb300 import lgnk
+    from oracle.objective import Problem as OP
+    from oracle.objective import gradient as ograd
+    im, vm = (13, 11, 9), (7, 6, 5)
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 0.9, 0.8)
+    op = OP(L.Grid(im, lo, hi), L.Grid(vm, lo, hi), K=3, N=64, model=model, alpha=1e-2, gamma=1e-3)
+    ctx = lgnk.Context(lgnk.Problem(image_m=im, velocity_m=vm, time_nodes=3, rk4_steps=64, model=model, alpha=1e-2,
+                                    gamma=1e-3, image_lo=lo, image_hi=hi))
+    rng = np.random.default_rng(11)
+    X = L.cell_centres(op.igrid)
+    T = np.exp(-((X[0] - 0.5) ** 2 + (X[1] - 0.45) ** 2 + (X[2] - 0.4) ** 2) / 0.03).reshape(op.igrid.shape)
+    R = np.roll(T, 1, axis=2)
+    g = synth.GridSpec(vm, lo, hi)
+    v = synth.random_velocity(g, 3, 0.15, 3)
+    dv = synth.random_velocity(g, 3, 0.05, 4)
+    r = rng.normal(size=T.shape)
+    f32 = {k: np.ascontiguousarray(a, dtype=np.float32) for k, a in dict(T=T, R=R, v=v, dv=dv, r=r).items()}
+    f64 = {k: a.astype(np.float64) for k, a in f32.items()}
+    t = {k: torch.from_numpy(a).cuda() for k, a in f32.items()}
+    args = (model, f64["v"], op.vgrid, f64["T"], op.igrid, 64)
+    assert rel(_np(ctx.forward(t["v"], t["T"])), L.final_state(*args)[0]) <= TOL
+    assert rel(_np(ctx.hessvec(t["v"], t["T"], t["dv"])), hessvec(op, f64["v"], f64["T"], f64["dv"])) <= TOL
+    if model == "transport":
+        assert rel(_np(ctx.jvp(t["v"], t["T"], t["dv"])), L.jvp(*args, f64["dv"])) <= TOL
+        assert rel(_np(ctx.jtvp(t["v"], t["T"], t["r"])), L.jtvp(*args, f64["r"])) <= TOL
+        _, _, _, gr = ctx.objective(t["v"], t["T"], t["R"], grad=True)
+        assert rel(_np(gr), ograd(op, f64["v"], f64["T"], f64["R"])) <= TOL
 
 
 def test_aliasing_and_shape_errors():
