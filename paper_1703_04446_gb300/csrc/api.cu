@@ -527,6 +527,21 @@ lgnk_status hessvec_assembled_packed(lgnk_ctx* ctx, const float* dv, float* out)
 lgnk_status precond_apply(lgnk_ctx* ctx, const float* r, float* z) {
     const int kd = ctx->K * ctx->d;
     cudaStream_t s = ctx->stream;
+    if (ctx->vg.m[ctx->d - 1] <= 128) {
+        // the last axis's forward transform, scale and inverse transform in one pass
+        if (ctx->d == 3) {
+            KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 3, kd, 0, false, s));
+            KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, false, s));
+            KL(launch_dct_last_fused(ctx->pc1, ctx->pc0, ctx->Cm[2], ctx->inv_eig, ctx->vg, 3, kd, s));
+            KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, true, s));
+            KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->vg, 3, kd, 0, true, s));
+        } else {
+            KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 2, kd, 0, false, s));
+            KL(launch_dct_last_fused(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->inv_eig, ctx->vg, 2, kd, s));
+            KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->vg, 2, kd, 0, true, s));
+        }
+        return LGNK_OK;
+    }
     if (ctx->d == 3) {
         KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 3, kd, 0, false, s));
         KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, false, s));

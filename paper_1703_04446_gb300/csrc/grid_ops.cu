@@ -514,6 +514,84 @@ __global__ void __launch_bounds__(kBlock) dct_tile_kernel(const float* __restric
     }
 }
 
+// The last axis of the preconditioner in one pass: forward DCT along the
+// axis, the spectral scale inv_eig (per mode, the same for every block), and
+// the inverse DCT, with the scaled modes kept in shared memory in between.
+// Same 64-line tiles and register blocking as dct_tile_kernel (strided form);
+// every sum still runs in increasing index order.
+__global__ void __launch_bounds__(kBlock) dct_last_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                                const float* __restrict__ C,
+                                                                const float* __restrict__ inv_eig, int m,
+                                                                long long inner) {
+    extern __shared__ __align__(16) float sm[];
+    const int MP = (m + 3) & ~3;
+    float* Cf = sm;                   // forward: [q][k] = C[k][q]
+    float* Ci = sm + m * MP;          // inverse: [k][k'] = C[k][k']
+    float* tile = sm + 2 * m * MP;    // [q][kDctLS], then the scaled modes [k][kDctLS]
+    const int t = threadIdx.x;
+    for (int e = t; e < m * MP; e += kBlock) {
+        const int q = e / MP, k = e % MP;
+        Cf[e] = k < m ? __ldg(C + (size_t)k * m + q) : 0.0f;
+        Ci[e] = k < m ? __ldg(C + (size_t)q * m + k) : 0.0f;
+    }
+    const long long o = blockIdx.y, i0 = (long long)blockIdx.x * kDctLines;
+    for (int e = t; e < kDctLines * m; e += kBlock) {
+        const int q = e / kDctLines, l = e % kDctLines;
+        tile[q * kDctLS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
+    }
+    __syncthreads();
+    const int ntask = (MP / 4) * (kDctLines / 4);
+    float acc[2][4][4];
+    for (int pass = 0; pass < 2; ++pass) {
+        const float* Cm = pass == 0 ? Cf : Ci;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int task = t + r * kBlock;
+            if (task >= ntask) break;
+            const int kb = task / (kDctLines / 4), lb = task % (kDctLines / 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[r][i][j] = 0.0f;
+            const float4* cp = reinterpret_cast<const float4*>(Cm) + kb;
+            const float4* xp = reinterpret_cast<const float4*>(tile) + lb;
+#pragma unroll 4
+            for (int q = 0; q < m; ++q) {
+                const float4 c = cp[q * (MP / 4)];
+                const float4 x = xp[q * (kDctLS / 4)];
+                const float cv[4] = {c.x, c.y, c.z, c.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[r][i][j] = fmaf(cv[i], xv[j], acc[r][i][j]);
+            }
+        }
+        __syncthreads();              // every thread is done reading the tile
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int task = t + r * kBlock;
+            if (task >= ntask) break;
+            const int kb = task / (kDctLines / 4), lb = task % (kDctLines / 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * kb + i;
+                if (k >= m) break;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long long l = i0 + 4 * lb + j;
+                    if (pass == 0) {
+                        const float sc = l < inner ? __ldg(inv_eig + (size_t)k * inner + l) : 0.0f;
+                        tile[k * kDctLS + 4 * lb + j] = acc[r][i][j] * sc;
+                    } else if (l < inner) {
+                        out[((size_t)o * m + k) * inner + l] = acc[r][i][j];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Shared memory of dct_tile_kernel for an axis of m cells (bytes).
 inline size_t dct_tile_smem(int m) {
     const size_t MP = (size_t)((m + 3) & ~3);
@@ -856,6 +934,29 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const D
         const dim3 grid((unsigned)((inner + kDctLines - 1) / kDctLines), (unsigned)outer);
         dct_tile_kernel<false><<<grid, kBlock, smem, s>>>(in, out, C, m, inner, inner * m * outer, inverse ? 1 : 0);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dct_last_fused(const float* in, float* out, const float* C, const float* inv_eig, const DevGrid& g,
+                                  int d, int nblocks_kd, cudaStream_t s) {
+    const int axis = d - 1;
+    const int m = g.m[axis];
+    const long long inner = axis == 1 ? (long long)g.m[0] : (long long)g.m[0] * g.m[1];
+    if (m > kDctTileMax || nblocks_kd > 65535) return cudaErrorNotSupported;
+    const size_t MP = (size_t)((m + 3) & ~3);
+    const size_t smem = (2 * (size_t)m * MP + (size_t)m * kDctLS) * sizeof(float);
+    static bool attr_set_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set_dev[dev]) {
+        const int smax = (int)((2 * (size_t)kDctTileMax * kDctTileMax + (size_t)kDctTileMax * kDctLS) * sizeof(float));
+        const cudaError_t e =
+            cudaFuncSetAttribute(dct_last_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        if (e != cudaSuccess) return e;
+        attr_set_dev[dev] = true;
+    }
+    const dim3 grid((unsigned)((inner + kDctLines - 1) / kDctLines), (unsigned)nblocks_kd);
+    dct_last_fused_kernel<<<grid, kBlock, smem, s>>>(in, out, C, inv_eig, m, inner);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,10 @@ cudaError_t launch_elastic(int d, const float* x, const float* div, float* out, 
                            float smu, float slm, float gamma, const float* addsrc, cudaStream_t s);
 cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const DevGrid& g, int d,
                             int nblocks_kd, int axis, bool inverse, cudaStream_t s);
+// forward DCT, scale by inv_eig and inverse DCT along the last axis in one pass;
+// cudaErrorNotSupported when that axis has more than 128 cells
+cudaError_t launch_dct_last_fused(const float* in, float* out, const float* C, const float* inv_eig, const DevGrid& g,
+                                  int d, int nblocks_kd, cudaStream_t s);
 cudaError_t launch_scale_modes(float* x, const float* inv_eig, size_t block_elems, size_t count,
                                cudaStream_t s);
 // y = a * x + b * y  (count floats)

@@ -953,6 +953,8 @@ __device__ __forceinline__ void write_row(const TraceArgs& A, const AsmTable<D>&
 // length (every row has at least one) and kept in registers for both the
 // gather and the scatter; further blocks are read in a loop (twice for HESS).
 constexpr int kEllRegBlocks = 1;
+// 128-thread CTAs (measured 0.116 -> 0.109 ms against 256 on the 128^3 matvec)
+constexpr int kEllBlock = 128;
 
 template <int D>
 __device__ __forceinline__ void ell_load(const EllArgs& A, long long i, int j, long long& key, float* b) {
@@ -995,7 +997,7 @@ __device__ __forceinline__ void ell_scatter(const EllArgs& A, long long key, con
 }
 
 template <int D, int EMODE>
-__global__ void __launch_bounds__(LGNK_BLOCK) ell_kernel(const EllArgs A) {
+__global__ void __launch_bounds__(kEllBlock) ell_kernel(const EllArgs A) {
     constexpr int B = (1 << D) * D;
     constexpr int RB = kEllRegBlocks;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1041,12 +1043,12 @@ __global__ void __launch_bounds__(LGNK_BLOCK) ell_kernel(const EllArgs A) {
 
 template <int D>
 static cudaError_t launch_ell_dim(int mode, const EllArgs& a, cudaStream_t s) {
-    const long long blocks = (a.M + LGNK_BLOCK - 1) / LGNK_BLOCK;
+    const long long blocks = (a.M + kEllBlock - 1) / kEllBlock;
     if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     switch (mode) {
-        case ELL_JVP: ell_kernel<D, ELL_JVP><<<(unsigned)blocks, LGNK_BLOCK, 0, s>>>(a); break;
-        case ELL_JTVP: ell_kernel<D, ELL_JTVP><<<(unsigned)blocks, LGNK_BLOCK, 0, s>>>(a); break;
-        case ELL_HESS: ell_kernel<D, ELL_HESS><<<(unsigned)blocks, LGNK_BLOCK, 0, s>>>(a); break;
+        case ELL_JVP: ell_kernel<D, ELL_JVP><<<(unsigned)blocks, kEllBlock, 0, s>>>(a); break;
+        case ELL_JTVP: ell_kernel<D, ELL_JTVP><<<(unsigned)blocks, kEllBlock, 0, s>>>(a); break;
+        case ELL_HESS: ell_kernel<D, ELL_HESS><<<(unsigned)blocks, kEllBlock, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
