@@ -496,7 +496,8 @@ def run_gpu(args):
         g_zero = rep_g0
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        _, reps = lgnk.lgnk_solve_multilevel(prob, tT, tR, 3, max_gn=args.max_gn, gn_grad_rtol=1e-3, max_pcg=50,
+        # (twice the single-level cap: from the coarse levels' minimum the finest level needs about 40 steps)
+        _, reps = lgnk.lgnk_solve_multilevel(prob, tT, tR, 3, max_gn=2 * args.max_gn, gn_grad_rtol=1e-3, max_pcg=50,
                                              pcg_rtol=0.1, gn_grad_atol=1e-3 * g_zero)
         torch.cuda.synchronize(dev)
         tts["multilevel_3"] = {"seconds": time.perf_counter() - t0,
