@@ -551,7 +551,9 @@ def profile_case(args):
     stationary velocity, N = 8, alpha = 1e-2.  'hess' launches the fused
     matrix-free matvec `launches` times; 'ell' assembles J once and then
     launches the assembled matvec `launches` times; 'solve' runs `launches`
-    Gauss-Newton iterations (every kernel of the solver)."""
+    Gauss-Newton iterations (every kernel of the solver); 'cont' launches the
+    mass-preserving matvec (9 time nodes, N = 16, as the brain-scale workload)
+    `launches` times."""
     import torch
     from paper_1703_04446_gb300 import lgnk, synth
     S = args.size
@@ -570,6 +572,18 @@ def profile_case(args):
         ctx.assemble(tv, tT)
         for _ in range(args.launches):
             ctx.hessvec_assembled(tdv, out=out)
+    elif args.profile_case == "cont":
+        # the mass-preserving matvec on the shape of the brain-scale workload's grids (9 time nodes, N = 16)
+        cprob = lgnk.Problem(image_m=(S,) * 3, velocity_m=(S // 2,) * 3, time_nodes=9, rk4_steps=16,
+                             model="continuity", alpha=1e-3)
+        cctx = lgnk.Context(cprob)
+        cv = torch.from_numpy(synth.random_velocity(vg, 9, 6 * h, 7).astype(np.float32)).cuda()
+        cdv = torch.from_numpy(synth.random_velocity(vg, 9, 2 * h, 5).astype(np.float32)).cuda()
+        rho = (tT / tT.sum()).contiguous()
+        cout = torch.empty_like(cdv)
+        for _ in range(args.launches):
+            cctx.hessvec(cv, rho, cdv, cout)
+        out = cout
     elif args.profile_case == "solve":
         # `launches` Gauss-Newton iterations from v = 0 towards the phantom moved by v
         R = ctx.forward(tv, tT)
@@ -594,7 +608,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true")
-    ap.add_argument("--profile-case", choices=["hess", "ell", "solve"], default=None,
+    ap.add_argument("--profile-case", choices=["hess", "ell", "solve", "cont"], default=None,
                     help="run only a short fixed invocation of one kernel (for ncu captures)")
     ap.add_argument("--size", type=int, default=128, help="image cells per axis of --profile-case")
     ap.add_argument("--launches", type=int, default=3, help="kernel launches of --profile-case")
