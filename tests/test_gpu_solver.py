@@ -64,3 +64,24 @@ def test_nonfinite_input_is_reported():
     with pytest.raises(lgnk.LgnkError) as e:
         ctx.objective(torch.zeros(prob.velocity_shape, device="cuda"), T, R)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("matvec", [0, 1])
+def test_device_loop_and_direct_launches_agree(matvec):
+    """The PCG loop as a device-side CUDA graph (the default) against direct
+    launches with a host read per iteration (the path taken while the
+    tracing kernels are profiled): the same iterations and the same minimum,
+    up to the order of float atomics in the gradient scatter."""
+    lgnk, prob, op, ins = _setup()
+    ctx = lgnk.Context(prob)
+    T, R = (torch.from_numpy(ins[k]).cuda() for k in ("T", "R"))
+    v_g, rep_g = ctx.solve(T, R, None, max_gn=6, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=1e-3, matvec=matvec)
+    ctx.profile(True)
+    v_d, rep_d = ctx.solve(T, R, None, max_gn=6, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=1e-3, matvec=matvec)
+    ms, traced, launches = ctx.profile_read()
+    ctx.profile(False)
+    assert traced > 0 and launches > traced
+    assert rep_d["gn_iters"] == rep_g["gn_iters"]
+    assert abs(rep_d["pcg_iters"] - rep_g["pcg_iters"]) <= 2
+    assert abs(rep_d["J"] - rep_g["J"]) <= 1e-4 * rep_g["J"]
+    assert float(torch.linalg.norm(v_d - v_g) / torch.linalg.norm(v_g)) <= 1e-3
