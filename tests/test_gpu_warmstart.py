@@ -132,3 +132,16 @@ def test_rejects_batches_over_the_maximum():
     with pytest.raises(lgnk.LgnkError):
         net._check(net.lib.lgnk_ws_predict(net.handle, 3, net._t(Tg, T.size, "T"), net._t(Rg, R.size, "R"),
                                            net._t(torch.empty(3 * 2 * 8 * 8, device="cuda"), 384, "v")))
+
+
+def test_pipeline_end_to_end_small():
+    """The whole learned-warm-start pipeline on a few pairs: solver-made
+    targets, training, then warm-started solves that reach the zero-start
+    solves' gradient norm (the solver stays the judge of the prediction)."""
+    from paper_1703_04446_gb300 import warmstart as WS
+    out = WS.run(n_train=16, n_test=4, channels=4, epochs=2, batch=8)
+    ev = out["eval"]
+    assert out["train_steps"] == 4 and out["loss_last"] > 0.0
+    assert ev["pairs"] == 4
+    assert ev["zero"]["converged"] >= 3 and ev["warm"]["converged"] >= ev["zero"]["converged"] - 1
+    assert ev["final_J_ratio_warm_over_zero"] == pytest.approx(1.0, rel=5e-2)
