@@ -609,6 +609,24 @@ __device__ __forceinline__ void stage_adjoint_cached(const DevGrid& g, const flo
     scatter_add<D>(g, S, s0, base, f, mu);
 }
 
+// The cached-cell form of stage_value (same arithmetic in the same order).
+template <int D>
+__device__ __forceinline__ void stage_value_cached(const DevGrid& g, const float* __restrict__ V, size_t s0,
+                                                   const int* p, const float* f, CellCache<D, false>& C, float* val) {
+    cache_cell<D, false>(g, V, nullptr, s0, linear<D>(g, p), C);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        float v0, dx, dy;
+        cell_plane<D>(C.v, 0, f, q, v0, dx, dy);
+        if (D == 3) {
+            float v1;
+            cell_plane<D>(C.v, 1, f, q, v1, dx, dy);
+            v0 = lerp(v0, v1, f[D - 1]);
+        }
+        val[q] = v0;
+    }
+}
+
 // T(y) and optionally grad T(y) from the padded image, y at displacement u.
 template <int D, bool GRAD>
 __device__ __forceinline__ float sample_image(const DevGrid& g, const Start<D>& s, const float* __restrict__ Tp,
@@ -758,8 +776,9 @@ __device__ __forceinline__ void step_slices(const TraceArgs& A, int k, size_t& s
 
 // One RK4 step of the characteristic (Alg. 1 without the derivative), on the
 // displacement u.
-template <int D, bool NS, bool REC>
-__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u, int k, float* rec) {
+template <int D, bool NS, bool REC, bool CACHE>
+__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u, int k, float* rec,
+                                         CellCache<D, false>& C) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -772,7 +791,8 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
         for (int a = 0; a < D; ++a) rec[a] = u[a];
     }
     locate<D>(A.vg, sv, u, p, f);
-    stage_value<D>(A.vg, V, s1, p, f, vs);
+    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s1, p, f, C, vs);
+    else stage_value<D>(A.vg, V, s1, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = vs[a]; us[a] = fmaf(hdt, vs[a], u[a]); }
     if (REC) {
@@ -780,7 +800,8 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
         for (int a = 0; a < D; ++a) rec[D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
-    stage_value<D>(A.vg, V, s2, p, f, vs);
+    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
+    else stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(hdt, vs[a], u[a]); }
     if (REC) {
@@ -788,7 +809,8 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
         for (int a = 0; a < D; ++a) rec[2 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
-    stage_value<D>(A.vg, V, s2, p, f, vs);
+    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
+    else stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(dt, vs[a], u[a]); }
     if (REC) {
@@ -796,7 +818,8 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
         for (int a = 0; a < D; ++a) rec[3 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
-    stage_value<D>(A.vg, V, s4, p, f, vs);
+    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s4, p, f, C, vs);
+    else stage_value<D>(A.vg, V, s4, p, f, vs);
     const float s6 = dt / 6.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) u[a] = fmaf(s6, acc[a] + vs[a], u[a]);
@@ -1071,9 +1094,11 @@ __device__ __forceinline__ double block_sum(double x) {
     return s;
 }
 
-// 256 threads; FWD at 64 registers (4 CTAs per SM), the derivative modes at 80
-// (3 CTAs): measured fastest among 64/80/128-register and 256/512-thread
-// configurations on the 128^3 matvec.
+// 256 threads; FWD at 64 registers (4 CTAs per SM; 80 registers, 3 CTAs, for
+// the 3D transport sweep with its value cell cache: 0.256 -> 0.226 ms on the
+// 128^3 image against the uncached sweep at 4 CTAs), the other derivative
+// modes at 80 (3 CTAs): measured fastest among 64/80/128-register and
+// 256/512-thread configurations on the 128^3 matvec.
 template <int D, int MODEL, int MODE>
 struct TraceOccupancy {
     // CTAs per SM the register budget is set for: the 3D transport modes hold
@@ -1083,7 +1108,7 @@ struct TraceOccupancy {
     // 0.82 ms with the scatter block as well; the assembly 1.23 -> 0.79 ms
     // from 3 to 2 CTAs with its pending block in registers)
     static constexpr int value =
-        MODE == MODE_FWD ? 4 : ((D == 3 && MODEL == LGNK_TRANSPORT) ? 2 : 3);
+        MODE == MODE_FWD ? ((D == 3 && MODEL == LGNK_TRANSPORT) ? 3 : 4) : ((D == 3 && MODEL == LGNK_TRANSPORT) ? 2 : 3);
 };
 
 template <int D, bool NS, int MODEL, int MODE>
@@ -1126,6 +1151,8 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
         }
         CellCache<D, true> tcache;
         tcache.key = -1;
+        CellCache<D, false> vcache;   // v corners for the forward and adjoint sweeps
+        vcache.key = -1;
         // stage positions of every step (recorded for the adjoint sweep)
         float hist[ADJOINT ? LGNK_MAX_STEPS : 1][4 * D];
 
@@ -1133,7 +1160,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
         for (int k = 0; k < A.N; ++k) {
             float* rec = hist[ADJOINT ? k : 0];
             if (TANGENT) rk4_tangent_step<D, NS, ADJOINT, CACHE>(A, V, dV, u, dy, k, rec, tcache);
-            else rk4_step<D, NS, ADJOINT>(A, V, u, k, rec);
+            else rk4_step<D, NS, ADJOINT, CACHE>(A, V, u, k, rec, vcache);
         }
         if (A.yout != nullptr) {
             const int M = A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
@@ -1219,11 +1246,9 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
         }
 
         if (ADJOINT) {
-            CellCache<D, false> acache;
-            acache.key = -1;
 #pragma unroll 1
             for (int k = A.N - 1; k >= 0; --k)
-                rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, hist[ADJOINT ? k : 0], lam, k, acache);
+                rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, hist[ADJOINT ? k : 0], lam, k, vcache);
             scatter_finish<D>(A.vg, S);
             if constexpr (MODE == MODE_ASM) {
                 write_row<D>(A, *S.tab, vox);
