@@ -167,8 +167,10 @@ lgnk_status lgnk_precond(lgnk_ctx* ctx, const float* r, float* z);
 lgnk_status lgnk_jacobian_determinant(lgnk_ctx* ctx, const float* v, const float* T, float* det,
                                       double* det_min, double* det_max);
 
-/* FP64 inner product of two device float arrays of length count; host result.
- * Synchronises the stream. */
+/* Inner product of two device float arrays of length count, summed in pairs
+ * of FP32 values with exact rounding errors (about 48 significant bits, a
+ * deterministic order) and returned in FP64 on the host.  Synchronises the
+ * stream. */
 lgnk_status lgnk_dot(lgnk_ctx* ctx, const float* a, const float* b, size_t count, double* out);
 
 /* Profiling.  lgnk_profile(ctx, 1) resets the counters and starts recording a
@@ -215,7 +217,7 @@ void lgnk_solve_opts_default(lgnk_solve_opts* opts);
 /* Inexact Gauss-Newton-Krylov with Armijo line search (Eq. 11): from the
  * initial v_inout[n] (device, overwritten with the result), minimise J for the
  * template T[M] and reference R[M].  Hessian products, preconditioner, vector
- * updates and FP64 inner products run on the device; the host drives the loop
+ * updates and inner products (FP32 pairs, about 48 bits) run on the device; the host drives the loop
  * and reads one scalar per reduction.  opts may be NULL (defaults); report may
  * be NULL.  Returns LGNK_OK on convergence, LGNK_NOT_CONVERGED at the GN cap,
  * LGNK_LS_FAILED when the line search stalls. */

@@ -1,11 +1,13 @@
 // Grid utilities of the lgnk library: layout conversion between the ABI layout
-// and the padded packed layout of the tracing kernels, FP64 reductions,
+// and the padded packed layout of the tracing kernels, reductions (FP32-pair
+// sums per element, FP64 from the block partials on),
 // regularizer stencils (Sec. 2.1, Sec. 3.2), the per-axis DCT of the spectral
 // preconditioner (Sec. 3.2) and the vector updates of PCG.
 #include <cmath>
 
 #include <algorithm>
 
+#include "fsum.cuh"
 #include "lgnk_internal.h"
 
 namespace {
@@ -155,14 +157,15 @@ __device__ __forceinline__ double block_reduce(double x) {
     return s;
 }
 
-// res = u1 - R (Eq. 10): FP64 partial sums of res^2 per block; rp (padded) = scale * res.
+// res = u1 - R (Eq. 10): partial sums of res^2 per block (FP64); rp (padded) = scale * res.
 __global__ void residual_kernel(const float* __restrict__ u1, const float* __restrict__ R, float* __restrict__ rp,
                                 DevGrid g, int d, float scale, double* partial) {
     const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
-    double s = 0.0;
+    fpair s = fpair_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
-        const float r = u1[i] - R[i];
-        s += (double)r * (double)r;
+        const float ui = u1[i], Ri = R[i];
+        const float r = ui - Ri;
+        fpair_add_sqdiff(s, ui, Ri);
         if (rp != nullptr) {
             const int x = (int)(i % g.m[0]);
             const int y = (int)((i / g.m[0]) % g.m[1]);
@@ -171,23 +174,23 @@ __global__ void residual_kernel(const float* __restrict__ u1, const float* __res
             rp[p] = scale * r;
         }
     }
-    s = block_reduce(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    s = fpair_block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = fpair_value(s);
 }
 
 __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b, size_t count, double* partial) {
-    double s = 0.0;
+    fpair s = fpair_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        s += (double)a[i] * (double)b[i];
-    s = block_reduce(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+        fpair_add_prod(s, a[i], b[i]);
+    s = fpair_block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = fpair_value(s);
 }
 
 // One or two inner products sharing the first operand, finished in the same
-// launch: every block writes its FP64 partial sums, and the last block to
-// finish (a counter, reset by that block) adds the partials in block order
-// (deterministic) into sc[slot_b] (a.b) and sc[slot_c] (a.c, when c is
-// given), then the PCG step lengths of step `mode` (-1: none) from the FP64
+// launch: every block writes its partial sums (FP32 pairs, stored in the FP64
+// partial buffer's slots), and the last block to finish (a counter, reset by
+// that block) adds the partials in a fixed order (deterministic) into
+// sc[slot_b] (a.b) and sc[slot_c] (a.c, when c is given), then the PCG step lengths of step `mode` (-1: none) from the FP64
 // inner products in sc ([2] p.Hp, [3] r.r, [4] r.z new, [5] r.z current):
 //   mode 0: alpha = rz / pHp, or 0 when pHp is not positive; f[0] = alpha, f[1] = -alpha
 //   mode 1: beta = rz_new / rz, then rz = rz_new;             f[2] = beta
@@ -206,40 +209,47 @@ __device__ __forceinline__ void pcg_step_lengths(double* sc, float* f, int mode)
 __global__ void dot_fused_kernel(const float* __restrict__ a, const float* __restrict__ b,
                                  const float* __restrict__ c, size_t count, double* partial, unsigned* counter,
                                  double* sc, int slot_b, int slot_c, int mode, float* f) {
-    double s = 0.0, t = 0.0;
+    fpair s = fpair_zero(), t = fpair_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const double ai = (double)a[i];
-        s += ai * (double)b[i];
-        if (c != nullptr) t += ai * (double)c[i];
+        const float ai = a[i];
+        fpair_add_prod(s, ai, b[i]);
+        if (c != nullptr) fpair_add_prod(t, ai, c[i]);
     }
-    s = block_reduce(s);
+    s = fpair_block_sum(s);
     if (c != nullptr) {
-        __syncthreads();      // block_reduce's shared slots are reused
-        t = block_reduce(t);
+        __syncthreads();      // fpair_block_sum's shared slots are reused
+        t = fpair_block_sum(t);
     }
+    float* pp = reinterpret_cast<float*>(partial);    // pair j at floats 2j, 2j + 1
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        partial[blockIdx.x] = s;
-        if (c != nullptr) partial[gridDim.x + blockIdx.x] = t;
+        pp[2 * blockIdx.x] = s.hi;
+        pp[2 * blockIdx.x + 1] = s.lo;
+        if (c != nullptr) {
+            pp[2 * (gridDim.x + blockIdx.x)] = t.hi;
+            pp[2 * (gridDim.x + blockIdx.x) + 1] = t.lo;
+        }
         __threadfence();
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double u = 0.0, w = 0.0;
+    const volatile float* vp = pp;
+    fpair u = fpair_zero(), w = fpair_zero();
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        u += ((volatile double*)partial)[i];
-        if (c != nullptr) w += ((volatile double*)partial)[gridDim.x + i];
+        fpair_add(u, fpair{vp[2 * i], vp[2 * i + 1]});
+        if (c != nullptr) fpair_add(w, fpair{vp[2 * (gridDim.x + i)], vp[2 * (gridDim.x + i) + 1]});
     }
-    u = block_reduce(u);
+    __syncthreads();          // the first phase's fpair_block_sum slots are reused
+    u = fpair_block_sum(u);
     if (c != nullptr) {
         __syncthreads();
-        w = block_reduce(w);
+        w = fpair_block_sum(w);
     }
     if (threadIdx.x == 0) {
-        sc[slot_b] = u;
-        if (c != nullptr) sc[slot_c] = w;
+        sc[slot_b] = fpair_value(u);
+        if (c != nullptr) sc[slot_c] = fpair_value(w);
         pcg_step_lengths(sc, f, mode);
         *counter = 0u;
     }

@@ -54,6 +54,7 @@
 
 #include <type_traits>
 
+#include "fsum.cuh"
 #include "lgnk_internal.h"
 
 namespace lgnk {
@@ -1077,23 +1078,6 @@ static cudaError_t launch_ell_dim(int mode, const EllArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ double block_sum(double x) {
-    __shared__ double red[32];
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = x;
-    __syncthreads();
-    double s = 0.0;
-    if (warp == 0) {
-        s = (lane < nw) ? red[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    }
-    return s;
-}
-
 // 256 threads; FWD at 64 registers (4 CTAs per SM; 80 registers, 3 CTAs, for
 // the 3D transport sweep with its value cell cache: 0.256 -> 0.226 ms on the
 // 128^3 image against the uncached sweep at 4 CTAs), the other derivative
@@ -1129,8 +1113,8 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
     int idx[3];
     voxel_index<D>(A, idx);
     const bool active = idx[0] < A.ig.m[0] && idx[1] < A.ig.m[1] && (D == 2 || idx[2] < A.ig.m[2]);
-    double ssd = 0.0;
-    double entries = 0.0;     // MODE_ASM: blocks of this thread's row
+    fpair ssd = fpair_zero();  // res^2 of this thread's voxel (FWD with R, OBJGRAD, ASM with R)
+    int entries = 0;           // MODE_ASM: blocks of this thread's row
 
     SC S;
     scatter_init<D>(S, A.G);
@@ -1179,10 +1163,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
             if (MODE == MODE_FWD) {
                 const float val = sample_image<D, false>(A.ig, si, A.Tp, u, nullptr);
                 A.u1[vox] = val;
-                if (A.R != nullptr) {
-                    const double r = (double)val - (double)A.R[vox];
-                    ssd = r * r;
-                }
+                if (A.R != nullptr) fpair_add_sqdiff(ssd, val, A.R[vox]);
             } else if (MODE == MODE_JVP) {
                 sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 float du = 0.0f;
@@ -1207,16 +1188,16 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = gT[a];
                 if (A.R != nullptr) {     // with the objective: SSD and the gradient's weights h^d res
-                    const double rd = (double)val - (double)A.R[vox];
-                    ssd = rd * rd;
-                    A.u1[vox] = A.cellvol * (float)rd;
+                    const float Rv = A.R[vox];
+                    fpair_add_sqdiff(ssd, val, Rv);
+                    A.u1[vox] = A.cellvol * (val - Rv);
                 }
             } else {  // MODE_OBJGRAD
                 const float val = sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 if (A.u1 != nullptr) A.u1[vox] = val;
-                const double rd = (double)val - (double)A.R[vox];
-                ssd = rd * rd;
-                const float s = A.cellvol * (float)rd;
+                const float Rv = A.R[vox];
+                fpair_add_sqdiff(ssd, val, Rv);
+                const float s = A.cellvol * (val - Rv);
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = s * gT[a];
             }
@@ -1252,21 +1233,21 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
             scatter_finish<D>(A.vg, S);
             if constexpr (MODE == MODE_ASM) {
                 write_row<D>(A, *S.tab, vox);
-                entries = (double)S.tab->n;
+                entries = S.tab->n;
             }
         }
     }
 
     if (MODE == MODE_OBJGRAD || MODE == MODE_FWD || MODE == MODE_ASM) {
         if (A.partial != nullptr) {
-            const double s = block_sum(ssd);
-            if (threadIdx.x == 0) A.partial[blockIdx.x] = s;
+            const fpair s = fpair_block_sum(ssd);
+            if (threadIdx.x == 0) A.partial[blockIdx.x] = fpair_value(s);
         }
     }
     if (MODE == MODE_ASM && A.cpartial != nullptr) {
-        __syncthreads();      // block_sum's shared slots are reused
-        const double c = block_sum(entries);
-        if (threadIdx.x == 0) A.cpartial[blockIdx.x] = c;
+        __syncthreads();      // fpair_block_sum's shared slots are reused
+        const fpair c = fpair_block_sum(fpair{(float)entries, 0.0f});   // exact: at most 256 x 16 blocks
+        if (threadIdx.x == 0) A.cpartial[blockIdx.x] = fpair_value(c);
     }
 }
 

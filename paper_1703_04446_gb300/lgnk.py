@@ -437,7 +437,7 @@ def lgnk_jacobian_determinant(ctx: Context, v, T, field=True):
 
 
 def lgnk_dot(ctx: Context, a, b):
-    """FP64 inner product of two float32 device tensors."""
+    """Inner product of two float32 device tensors (FP32-pair sums, about 48 bits), as a Python float."""
     if a.numel() != b.numel():
         raise ValueError("size mismatch")
     for t in (a, b):

@@ -120,11 +120,25 @@ def test_adjoint_identity_on_gpu(name):
     assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs))
 
 
-def test_dot_is_fp64():
+def test_dot_accumulates_beyond_fp32():
+    """Inner products are summed in FP32 pairs (hi + lo with exact rounding
+    errors): a sum that FP32 alone would round is exact, and a random ragged
+    case lands within 1e-12 of sum |a_i b_i| from the exactly rounded sum of the
+    exact FP64 products (FP32 accumulation misses by about 3e-8 here)."""
+    import math
     ctx, t = _gpu("2d_transport_64")
     a = torch.full((1 << 20,), 1.0 + 2.0 ** -20, device="cuda")
     b = torch.full((1 << 20,), 3.0, device="cuda")
     assert ctx.dot(a, b) == pytest.approx(3.0 * (1.0 + 2.0 ** -20) * (1 << 20), rel=1e-15)
+    rng = np.random.default_rng(11)
+    n = (1 << 20) + 123
+    x = rng.normal(size=n).astype(np.float32) * np.exp(rng.uniform(-8, 8, size=n)).astype(np.float32)
+    y = (-x * (1.0 + 1e-6 * rng.normal(size=n))).astype(np.float32)
+    y[::7] = rng.normal(size=y[::7].size).astype(np.float32)
+    prods = x.astype(np.float64) * y.astype(np.float64)        # exact
+    ref = math.fsum(prods)
+    got = ctx.dot(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    assert abs(got - ref) <= 1e-12 * float(np.abs(prods).sum())
 
 
 def test_zero_velocity_is_identity():
