@@ -44,6 +44,9 @@ struct lgnk_ctx {
     void *Vp = nullptr, *dVp = nullptr, *Gp = nullptr;
     float *Tp = nullptr, *acc = nullptr, *rp = nullptr, *itmp = nullptr, *rtmp = nullptr;
     float *pc0 = nullptr, *pc1 = nullptr, *Cm[3] = {nullptr, nullptr, nullptr}, *inv_eig = nullptr;
+    // the DCT matrices in the shared-memory layouts of the tiled kernels, rows
+    // padded to P = m rounded up to 4: forward Cf[q][k] = C[k][q], inverse Ci[q][k] = C[q][k]
+    float *Cf[3] = {nullptr, nullptr, nullptr}, *Ci[3] = {nullptr, nullptr, nullptr};
     double* partial = nullptr;
     double* cpartial = nullptr;   // per-block entry counts of the assembled rows
     int npartial = 0;
@@ -529,15 +532,21 @@ lgnk_status precond_apply(lgnk_ctx* ctx, const float* r, float* z) {
     cudaStream_t s = ctx->stream;
     if (ctx->vg.m[ctx->d - 1] <= 128) {
         // the last axis's forward transform, scale and inverse transform in one pass
-        if (ctx->d == 3) {
+        if (ctx->d == 3 && ctx->vg.m[0] <= 64 && ctx->vg.m[1] <= 64) {
+            // y and x of each xy plane in one pass each way: three launches
+            const long long planes = (long long)kd * ctx->vg.m[2];
+            KL(launch_dct_plane(r, ctx->pc0, ctx->Cf[0], ctx->Cf[1], ctx->vg, planes, s));
+            KL(launch_dct_last_fused(ctx->pc0, ctx->pc1, ctx->Cf[2], ctx->Ci[2], ctx->inv_eig, ctx->vg, 3, kd, s));
+            KL(launch_dct_plane(ctx->pc1, z, ctx->Ci[0], ctx->Ci[1], ctx->vg, planes, s));
+        } else if (ctx->d == 3) {
             KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 3, kd, 0, false, s));
             KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, false, s));
-            KL(launch_dct_last_fused(ctx->pc1, ctx->pc0, ctx->Cm[2], ctx->inv_eig, ctx->vg, 3, kd, s));
+            KL(launch_dct_last_fused(ctx->pc1, ctx->pc0, ctx->Cf[2], ctx->Ci[2], ctx->inv_eig, ctx->vg, 3, kd, s));
             KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, true, s));
             KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->vg, 3, kd, 0, true, s));
         } else {
             KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 2, kd, 0, false, s));
-            KL(launch_dct_last_fused(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->inv_eig, ctx->vg, 2, kd, s));
+            KL(launch_dct_last_fused(ctx->pc0, ctx->pc1, ctx->Cf[1], ctx->Ci[1], ctx->inv_eig, ctx->vg, 2, kd, s));
             KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->vg, 2, kd, 0, true, s));
         }
         return LGNK_OK;
@@ -700,8 +709,12 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     if ((s = dalloc(ctx, ctx->n, &ctx->rtmp)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, ctx->n, &ctx->pc0)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, ctx->n, &ctx->pc1)) != LGNK_OK) return fail(s);
-    for (int a = 0; a < d; ++a)
-        if ((s = dalloc(ctx, (size_t)ctx->vg.m[a] * ctx->vg.m[a], &ctx->Cm[a])) != LGNK_OK) return fail(s);
+    for (int a = 0; a < d; ++a) {
+        const size_t m = (size_t)ctx->vg.m[a], P = (m + 3) & ~(size_t)3;
+        if ((s = dalloc(ctx, m * m, &ctx->Cm[a])) != LGNK_OK) return fail(s);
+        if ((s = dalloc(ctx, m * P, &ctx->Cf[a])) != LGNK_OK) return fail(s);
+        if ((s = dalloc(ctx, m * P, &ctx->Ci[a])) != LGNK_OK) return fail(s);
+    }
     if ((s = dalloc(ctx, ctx->Mv, &ctx->inv_eig)) != LGNK_OK) return fail(s);
     ctx->npartial = ctx->trace_blocks > 1280 ? ctx->trace_blocks : 1280;  // >= 2 x 608 min/max partials
     if ((s = dalloc(ctx, (size_t)ctx->npartial, &ctx->partial)) != LGNK_OK) return fail(s);
@@ -736,6 +749,16 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
                 hostC[(size_t)k * m + i] =
                     (float)(std::sqrt((k == 0 ? 1.0 : 2.0) / m) * std::cos(M_PI * k * (2 * i + 1) / (2.0 * m)));
         if (cudaMemcpy(ctx->Cm[a], hostC.data(), hostC.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(LGNK_ERR_CUDA);
+        const size_t P = ((size_t)m + 3) & ~(size_t)3;
+        std::vector<float> hf((size_t)m * P, 0.0f), hi((size_t)m * P, 0.0f);
+        for (int q = 0; q < m; ++q)
+            for (int k = 0; k < m; ++k) {
+                hf[(size_t)q * P + k] = hostC[(size_t)k * m + q];
+                hi[(size_t)q * P + k] = hostC[(size_t)q * m + k];
+            }
+        if (cudaMemcpy(ctx->Cf[a], hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ctx->Ci[a], hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(LGNK_ERR_CUDA);
     }
     std::vector<double> pv(ctx->Mv);

@@ -418,6 +418,19 @@ __global__ void dct_axis_kernel(const float* __restrict__ in, float* __restrict_
     }
 }
 
+// 16-byte asynchronous copy from global to shared memory (both addresses
+// 16-byte aligned), cached in L2 only; cp_async_wait_all() waits for every
+// copy this thread issued.  A CTA issues all its staging copies before the
+// first wait, so a tile arrives in about one memory round trip.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // The same transform for axes of at most kDctTileMax cells, as a small
 // register-blocked matrix product staged in shared memory.  Each array block
 // is viewed as [outer][m][inner] (inner = product of the cell counts of the
@@ -527,38 +540,53 @@ __global__ void __launch_bounds__(kBlock) dct_tile_kernel(const float* __restric
 // The last axis of the preconditioner in one pass: forward DCT along the
 // axis, the spectral scale inv_eig (per mode, the same for every block), and
 // the inverse DCT, with the scaled modes kept in shared memory in between.
-// Same 64-line tiles and register blocking as dct_tile_kernel (strided form);
-// every sum still runs in increasing index order.
-__global__ void __launch_bounds__(kBlock) dct_last_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                                const float* __restrict__ C,
-                                                                const float* __restrict__ inv_eig, int m,
-                                                                long long inner) {
+// LINES lines per CTA of 4 LINES threads, with the register blocking of
+// dct_tile_kernel (strided form); every sum still runs in increasing index
+// order.
+constexpr int kDctFusedLines = 32;
+
+template <int LINES>
+__global__ void __launch_bounds__(4 * LINES) dct_last_fused_kernel(const float* __restrict__ in,
+                                                                   float* __restrict__ out,
+                                                                   const float* __restrict__ Cfg,
+                                                                   const float* __restrict__ Cig,
+                                                                   const float* __restrict__ inv_eig, int m,
+                                                                   long long inner, int vec_in) {
+    constexpr int NT = 4 * LINES, LS = LINES + 4;
     extern __shared__ __align__(16) float sm[];
     const int MP = (m + 3) & ~3;
     float* Cf = sm;                   // forward: [q][k] = C[k][q]
     float* Ci = sm + m * MP;          // inverse: [k][k'] = C[k][k']
-    float* tile = sm + 2 * m * MP;    // [q][kDctLS], then the scaled modes [k][kDctLS]
+    float* tile = sm + 2 * m * MP;    // [q][LS], then the scaled modes [k][LS]
     const int t = threadIdx.x;
-    for (int e = t; e < m * MP; e += kBlock) {
-        const int q = e / MP, k = e % MP;
-        Cf[e] = k < m ? __ldg(C + (size_t)k * m + q) : 0.0f;
-        Ci[e] = k < m ? __ldg(C + (size_t)q * m + k) : 0.0f;
+    for (int e = t; e < m * MP / 4; e += NT) {
+        cp_async16(Cf + 4 * e, Cfg + 4 * e);
+        cp_async16(Ci + 4 * e, Cig + 4 * e);
     }
-    const long long o = blockIdx.y, i0 = (long long)blockIdx.x * kDctLines;
-    for (int e = t; e < kDctLines * m; e += kBlock) {
-        const int q = e / kDctLines, l = e % kDctLines;
-        tile[q * kDctLS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
+    const long long o = blockIdx.y, i0 = (long long)blockIdx.x * LINES;
+    if (vec_in) {                     // inner a multiple of 4, in 16-byte aligned: whole float4s in or out
+        for (int e = t; e < m * (LINES / 4); e += NT) {
+            const int q = e / (LINES / 4), l = 4 * (e % (LINES / 4));
+            if (i0 + l < inner) cp_async16(tile + q * LS + l, in + ((size_t)o * m + q) * inner + i0 + l);
+            else *reinterpret_cast<float4*>(tile + q * LS + l) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    } else {
+        for (int e = t; e < LINES * m; e += NT) {
+            const int q = e / LINES, l = e % LINES;
+            tile[q * LS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
-    const int ntask = (MP / 4) * (kDctLines / 4);
-    float acc[2][4][4];
+    const int ntask = (MP / 4) * (LINES / 4);
+    float acc[2][4][4];               // at most two tasks per thread (MP <= 128)
     for (int pass = 0; pass < 2; ++pass) {
         const float* Cm = pass == 0 ? Cf : Ci;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            const int task = t + r * kBlock;
+            const int task = t + r * NT;
             if (task >= ntask) break;
-            const int kb = task / (kDctLines / 4), lb = task % (kDctLines / 4);
+            const int kb = task / (LINES / 4), lb = task % (LINES / 4);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -568,7 +596,7 @@ __global__ void __launch_bounds__(kBlock) dct_last_fused_kernel(const float* __r
 #pragma unroll 4
             for (int q = 0; q < m; ++q) {
                 const float4 c = cp[q * (MP / 4)];
-                const float4 x = xp[q * (kDctLS / 4)];
+                const float4 x = xp[q * (LS / 4)];
                 const float cv[4] = {c.x, c.y, c.z, c.w}, xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -579,9 +607,9 @@ __global__ void __launch_bounds__(kBlock) dct_last_fused_kernel(const float* __r
         __syncthreads();              // every thread is done reading the tile
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            const int task = t + r * kBlock;
+            const int task = t + r * NT;
             if (task >= ntask) break;
-            const int kb = task / (kDctLines / 4), lb = task % (kDctLines / 4);
+            const int kb = task / (LINES / 4), lb = task % (LINES / 4);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int k = 4 * kb + i;
@@ -591,7 +619,7 @@ __global__ void __launch_bounds__(kBlock) dct_last_fused_kernel(const float* __r
                     const long long l = i0 + 4 * lb + j;
                     if (pass == 0) {
                         const float sc = l < inner ? __ldg(inv_eig + (size_t)k * inner + l) : 0.0f;
-                        tile[k * kDctLS + 4 * lb + j] = acc[r][i][j] * sc;
+                        tile[k * LS + 4 * lb + j] = acc[r][i][j] * sc;
                     } else if (l < inner) {
                         out[((size_t)o * m + k) * inner + l] = acc[r][i][j];
                     }
@@ -600,6 +628,118 @@ __global__ void __launch_bounds__(kBlock) dct_last_fused_kernel(const float* __r
         }
         __syncthreads();
     }
+}
+
+// The y and x axes of the transform on whole xy planes (both at most
+// kDctPlaneMax cells): a CTA holds one plane of one (block, z) in shared
+// memory and applies the y axis and then the x axis, two small matrix products
+// chained through shared memory.  The y result goes back transposed, [x][k],
+// from registers, so that both products read float4 rows of shared memory and
+// the plane is loaded and stored row-major.  With Ay, Ax the padded tables of
+// the direction (forward Cf, inverse Ci):
+//   forward: modes = C_y X C_x^T      inverse: X = C_y^T modes C_x
+// The tables and the plane are staged with asynchronous 16-byte copies, all
+// issued before the first wait.  A thread computes a 4 x 4 block of each
+// product; every sum runs over its index in increasing order.  The two axes
+// commute, so this equals the per-axis passes up to rounding.
+constexpr int kDctPlaneMax = 64;
+
+__global__ void __launch_bounds__(kBlock) dct_plane_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                           const float* __restrict__ Axg,
+                                                           const float* __restrict__ Ayg, int mx, int my,
+                                                           int vec_in, int vec_out) {
+    extern __shared__ __align__(16) float sm[];
+    const int PX = (mx + 3) & ~3, PY = (my + 3) & ~3;
+    const int LS = PX + 4, LT = PY + 4;   // row strides of the plane [y][x] and of the transposed result [x][k]
+    float* Ay = sm;                       // [q][PY]
+    float* Ax = Ay + my * PY;             // [q][PX]
+    float* S = Ax + mx * PX;              // the plane, later the y result transposed
+    const int t = threadIdx.x;
+    for (int e = t; e < my * PY / 4; e += kBlock) cp_async16(Ay + 4 * e, Ayg + 4 * e);
+    for (int e = t; e < mx * PX / 4; e += kBlock) cp_async16(Ax + 4 * e, Axg + 4 * e);
+    const size_t base = (size_t)blockIdx.x * mx * my;
+    if (vec_in) {                         // mx a multiple of 4 (PX = mx), in 16-byte aligned
+        const int c4 = mx / 4;
+        for (int e = t; e < my * c4; e += kBlock) {
+            const int y = e / c4, x = 4 * (e % c4);
+            cp_async16(S + y * LS + x, in + base + (size_t)y * mx + x);
+        }
+    } else {
+        for (int e = t; e < my * PX; e += kBlock) {
+            const int y = e / PX, x = e % PX;
+            S[y * LS + x] = x < mx ? __ldg(in + base + (size_t)y * mx + x) : 0.0f;
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int nxb = PX / 4;
+    const bool act = t < (PY / 4) * nxb;  // at most 256 blocks of 4 x 4: one per thread
+    const int kb = act ? t / nxb : 0, xb = act ? t % nxb : 0;
+    float acc[4][4];                      // [k along y][x]
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    if (act) {
+        const float4* ap = reinterpret_cast<const float4*>(Ay) + kb;
+        const float4* sp = reinterpret_cast<const float4*>(S) + xb;
+#pragma unroll 4
+        for (int q = 0; q < my; ++q) {
+            const float4 a = ap[q * (PY / 4)];
+            const float4 x = sp[q * (LS / 4)];
+            const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+        }
+    }
+    __syncthreads();                      // every read of the plane is done
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4*>(S + (4 * xb + j) * LT + 4 * kb) =
+                make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+    }
+    __syncthreads();
+    if (!act) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;   // now [k along x][y]
+    {
+        const float4* ap = reinterpret_cast<const float4*>(Ax) + xb;
+        const float4* tp = reinterpret_cast<const float4*>(S) + kb;
+#pragma unroll 4
+        for (int q = 0; q < mx; ++q) {
+            const float4 a = ap[q * (PX / 4)];
+            const float4 x = tp[q * (LT / 4)];
+            const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int y = 4 * kb + j;
+        if (y >= my) break;
+        float* o = out + base + (size_t)y * mx + 4 * xb;
+        if (vec_out) {
+            *reinterpret_cast<float4*>(o) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (4 * xb + i < mx) o[i] = acc[i][j];
+        }
+    }
+}
+
+inline size_t dct_plane_smem(int mx, int my) {
+    const size_t PX = (size_t)((mx + 3) & ~3), PY = (size_t)((my + 3) & ~3);
+    const size_t plane = std::max((size_t)my * (PX + 4), PX * (PY + 4));
+    return ((size_t)my * PY + (size_t)mx * PX + plane) * sizeof(float);
 }
 
 // Shared memory of dct_tile_kernel for an axis of m cells (bytes).
@@ -947,26 +1087,48 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const D
     return cudaGetLastError();
 }
 
-cudaError_t launch_dct_last_fused(const float* in, float* out, const float* C, const float* inv_eig, const DevGrid& g,
-                                  int d, int nblocks_kd, cudaStream_t s) {
+cudaError_t launch_dct_plane(const float* in, float* out, const float* Ax, const float* Ay, const DevGrid& g,
+                             long long planes, cudaStream_t s) {
+    const int mx = g.m[0], my = g.m[1];
+    if (mx > kDctPlaneMax || my > kDctPlaneMax || planes < 1 || planes > 0x7fffffffLL) return cudaErrorNotSupported;
+    static bool attr_set_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set_dev[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(dct_plane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)dct_plane_smem(kDctPlaneMax, kDctPlaneMax));
+        if (e != cudaSuccess) return e;
+        attr_set_dev[dev] = true;
+    }
+    const int vec_in = (mx % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0) ? 1 : 0;
+    const int vec_out = (mx % 4 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
+    dct_plane_kernel<<<(unsigned)planes, kBlock, dct_plane_smem(mx, my), s>>>(in, out, Ax, Ay, mx, my, vec_in,
+                                                                              vec_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dct_last_fused(const float* in, float* out, const float* Cf, const float* Ci, const float* inv_eig,
+                                  const DevGrid& g, int d, int nblocks_kd, cudaStream_t s) {
+    constexpr int L = kDctFusedLines;
     const int axis = d - 1;
     const int m = g.m[axis];
     const long long inner = axis == 1 ? (long long)g.m[0] : (long long)g.m[0] * g.m[1];
     if (m > kDctTileMax || nblocks_kd > 65535) return cudaErrorNotSupported;
     const size_t MP = (size_t)((m + 3) & ~3);
-    const size_t smem = (2 * (size_t)m * MP + (size_t)m * kDctLS) * sizeof(float);
+    const size_t smem = (2 * (size_t)m * MP + (size_t)m * (L + 4)) * sizeof(float);
     static bool attr_set_dev[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set_dev[dev]) {
-        const int smax = (int)((2 * (size_t)kDctTileMax * kDctTileMax + (size_t)kDctTileMax * kDctLS) * sizeof(float));
+        const int smax = (int)((2 * (size_t)kDctTileMax * kDctTileMax + (size_t)kDctTileMax * (L + 4)) * sizeof(float));
         const cudaError_t e =
-            cudaFuncSetAttribute(dct_last_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+            cudaFuncSetAttribute(dct_last_fused_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         if (e != cudaSuccess) return e;
         attr_set_dev[dev] = true;
     }
-    const dim3 grid((unsigned)((inner + kDctLines - 1) / kDctLines), (unsigned)nblocks_kd);
-    dct_last_fused_kernel<<<grid, kBlock, smem, s>>>(in, out, C, inv_eig, m, inner);
+    const dim3 grid((unsigned)((inner + L - 1) / L), (unsigned)nblocks_kd);
+    const int vec_in = (inner % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0) ? 1 : 0;
+    dct_last_fused_kernel<L><<<grid, 4 * L, smem, s>>>(in, out, Cf, Ci, inv_eig, m, inner, vec_in);
     return cudaGetLastError();
 }
 

@@ -142,10 +142,18 @@ cudaError_t launch_elastic(int d, const float* x, const float* div, float* out, 
                            float smu, float slm, float gamma, const float* addsrc, cudaStream_t s);
 cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const DevGrid& g, int d,
                             int nblocks_kd, int axis, bool inverse, cudaStream_t s);
-// forward DCT, scale by inv_eig and inverse DCT along the last axis in one pass;
-// cudaErrorNotSupported when that axis has more than 128 cells
-cudaError_t launch_dct_last_fused(const float* in, float* out, const float* C, const float* inv_eig, const DevGrid& g,
-                                  int d, int nblocks_kd, cudaStream_t s);
+// Padded DCT tables per axis (rows of P = m rounded up to 4 floats, zero past
+// m): forward Cf[q][k] = C[k][q], inverse Ci[q][k] = C[q][k].
+// The y and x axes of the spectral transform on whole xy planes (3D, both
+// axes at most 64 cells) with the tables of one direction (Cf or Ci of the x
+// and y axes): planes = blocks x z-planes.  cudaErrorNotSupported for larger
+// planes (the per-axis kernels cover them).
+cudaError_t launch_dct_plane(const float* in, float* out, const float* Ax, const float* Ay, const DevGrid& g,
+                             long long planes, cudaStream_t s);
+// forward DCT, scale by inv_eig and inverse DCT along the last axis in one pass
+// (the axis's Cf and Ci); cudaErrorNotSupported when that axis has more than 128 cells
+cudaError_t launch_dct_last_fused(const float* in, float* out, const float* Cf, const float* Ci, const float* inv_eig,
+                                  const DevGrid& g, int d, int nblocks_kd, cudaStream_t s);
 cudaError_t launch_scale_modes(float* x, const float* inv_eig, size_t block_elems, size_t count,
                                cudaStream_t s);
 // y = a * x + b * y  (count floats)

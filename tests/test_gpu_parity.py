@@ -95,10 +95,13 @@ def test_preconditioner(name):
     assert rel(_np(ctx.precond(t["dv"])), _oracle(name)["prec"]) <= TOL
 
 
-@pytest.mark.parametrize("vm,K", [((130, 20), 2), ((40, 36, 129), 1), ((128, 128), 1)])
+@pytest.mark.parametrize("vm,K", [((130, 20), 2), ((40, 36, 129), 1), ((128, 128), 1), ((64, 64, 64), 1),
+                                  ((64, 61, 33), 2), ((37, 64, 16), 1), ((65, 40, 20), 1)])
 def test_preconditioner_axis_lengths(vm, K):
     """Axes of more than 128 cells take the untiled DCT kernel, the others the
-    shared-memory tile (128 is the largest tiled length)."""
+    shared-memory tile (128 is the largest tiled length); 3D xy planes of at
+    most 64 x 64 cells take the plane kernel (float4 stores when x is a
+    multiple of 4, scalar ones otherwise), wider ones the per-axis tiles."""
     from oracle import lagrangian as Lg
     from oracle.objective import Problem as OProblem
     from paper_1703_04446_gb300 import lgnk
