@@ -539,32 +539,32 @@ lgnk_status precond_apply(lgnk_ctx* ctx, const float* r, float* z) {
             KL(launch_dct_last_fused(ctx->pc0, ctx->pc1, ctx->Cf[2], ctx->Ci[2], ctx->inv_eig, ctx->vg, 3, kd, s));
             KL(launch_dct_plane(ctx->pc1, z, ctx->Ci[0], ctx->Ci[1], ctx->vg, planes, s));
         } else if (ctx->d == 3) {
-            KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 3, kd, 0, false, s));
-            KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, false, s));
+            KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->Cf[0], ctx->vg, 3, kd, 0, false, s));
+            KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->Cf[1], ctx->vg, 3, kd, 1, false, s));
             KL(launch_dct_last_fused(ctx->pc1, ctx->pc0, ctx->Cf[2], ctx->Ci[2], ctx->inv_eig, ctx->vg, 3, kd, s));
-            KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, true, s));
-            KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->vg, 3, kd, 0, true, s));
+            KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->Ci[1], ctx->vg, 3, kd, 1, true, s));
+            KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->Ci[0], ctx->vg, 3, kd, 0, true, s));
         } else {
-            KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 2, kd, 0, false, s));
+            KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->Cf[0], ctx->vg, 2, kd, 0, false, s));
             KL(launch_dct_last_fused(ctx->pc0, ctx->pc1, ctx->Cf[1], ctx->Ci[1], ctx->inv_eig, ctx->vg, 2, kd, s));
-            KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->vg, 2, kd, 0, true, s));
+            KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->Ci[0], ctx->vg, 2, kd, 0, true, s));
         }
         return LGNK_OK;
     }
     if (ctx->d == 3) {
-        KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 3, kd, 0, false, s));
-        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 3, kd, 1, false, s));
-        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[2], ctx->vg, 3, kd, 2, false, s));
+        KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->Cf[0], ctx->vg, 3, kd, 0, false, s));
+        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->Cf[1], ctx->vg, 3, kd, 1, false, s));
+        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[2], ctx->Cf[2], ctx->vg, 3, kd, 2, false, s));
         KL(launch_scale_modes(ctx->pc0, ctx->inv_eig, ctx->Mv, ctx->n, s));
-        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[2], ctx->vg, 3, kd, 2, true, s));
-        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[1], ctx->vg, 3, kd, 1, true, s));
-        KL(launch_dct_axis(ctx->pc0, z, ctx->Cm[0], ctx->vg, 3, kd, 0, true, s));
+        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[2], ctx->Ci[2], ctx->vg, 3, kd, 2, true, s));
+        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[1], ctx->Ci[1], ctx->vg, 3, kd, 1, true, s));
+        KL(launch_dct_axis(ctx->pc0, z, ctx->Cm[0], ctx->Ci[0], ctx->vg, 3, kd, 0, true, s));
     } else {
-        KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->vg, 2, kd, 0, false, s));
-        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->vg, 2, kd, 1, false, s));
+        KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->Cf[0], ctx->vg, 2, kd, 0, false, s));
+        KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->Cf[1], ctx->vg, 2, kd, 1, false, s));
         KL(launch_scale_modes(ctx->pc1, ctx->inv_eig, ctx->Mv, ctx->n, s));
-        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[1], ctx->vg, 2, kd, 1, true, s));
-        KL(launch_dct_axis(ctx->pc0, z, ctx->Cm[0], ctx->vg, 2, kd, 0, true, s));
+        KL(launch_dct_axis(ctx->pc1, ctx->pc0, ctx->Cm[1], ctx->Ci[1], ctx->vg, 2, kd, 1, true, s));
+        KL(launch_dct_axis(ctx->pc0, z, ctx->Cm[0], ctx->Ci[0], ctx->vg, 2, kd, 0, true, s));
     }
     return LGNK_OK;
 }

@@ -447,21 +447,16 @@ constexpr int kDctLS = kDctLines + 4;        // tile row stride (float4-aligned)
 
 template <bool XAXIS>
 __global__ void __launch_bounds__(kBlock) dct_tile_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                          const float* __restrict__ C, int m, long long inner,
-                                                          long long lines, int inverse) {
+                                                          const float* __restrict__ Ctg, int m, long long inner,
+                                                          long long lines, int vec_in) {
     extern __shared__ __align__(16) float sm[];
     const int MP = (m + 3) & ~3;                 // k padded to whole float4s
-    float* Ct = sm;                              // [q][MP]
+    float* Ct = sm;                              // [q][MP]: the padded table of the direction (Cf or Ci)
     float* tile = sm + m * MP;                   // [q][kDctLS], later the output stage of axis 0
     const int t = threadIdx.x;
-    for (int e = t; e < m * MP; e += kBlock) {
-        const int q = e / MP, k = e % MP;
-        float c = 0.0f;
-        if (k < m) c = inverse ? __ldg(C + (size_t)q * m + k) : __ldg(C + (size_t)k * m + q);
-        Ct[e] = c;
-    }
+    for (int e = t; e < m * MP / 4; e += kBlock) cp_async16(Ct + 4 * e, Ctg + 4 * e);
     long long o = 0, i0 = 0, r0 = 0;
-    if (XAXIS) {
+    if (XAXIS) {                                 // lines are rows: loaded transposed, element by element
         r0 = (long long)blockIdx.x * kDctLines;
         for (int e = t; e < kDctLines * m; e += kBlock) {
             const int l = e / m, q = e % m;
@@ -470,11 +465,20 @@ __global__ void __launch_bounds__(kBlock) dct_tile_kernel(const float* __restric
     } else {
         o = blockIdx.y;
         i0 = (long long)blockIdx.x * kDctLines;
-        for (int e = t; e < kDctLines * m; e += kBlock) {
-            const int q = e / kDctLines, l = e % kDctLines;
-            tile[q * kDctLS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
+        if (vec_in) {                            // inner a multiple of 4, in 16-byte aligned
+            for (int e = t; e < m * (kDctLines / 4); e += kBlock) {
+                const int q = e / (kDctLines / 4), l = 4 * (e % (kDctLines / 4));
+                if (i0 + l < inner) cp_async16(tile + q * kDctLS + l, in + ((size_t)o * m + q) * inner + i0 + l);
+                else *reinterpret_cast<float4*>(tile + q * kDctLS + l) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        } else {
+            for (int e = t; e < kDctLines * m; e += kBlock) {
+                const int q = e / kDctLines, l = e % kDctLines;
+                tile[q * kDctLS + l] = (i0 + l < inner) ? __ldg(in + ((size_t)o * m + q) * inner + i0 + l) : 0.0f;
+            }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     const int ntask = (MP / 4) * (kDctLines / 4);
     constexpr int SS = kDctTileMax + 1;          // output stage row stride (axis 0)
@@ -1042,8 +1046,8 @@ cudaError_t launch_elastic(int d, const float* x, const float* div, float* out, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const DevGrid& g, int d, int nblocks_kd,
-                            int axis, bool inverse, cudaStream_t s) {
+cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const float* Cp, const DevGrid& g, int d,
+                            int nblocks_kd, int axis, bool inverse, cudaStream_t s) {
     (void)d;
     const size_t total = (size_t)g.m[0] * g.m[1] * g.m[2] * nblocks_kd;
     const int m = g.m[axis];
@@ -1069,7 +1073,7 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const D
         }
         const long long rows = outer;   // inner = 1: every (y, z, block) is one line
         dct_tile_kernel<true><<<(unsigned)((rows + kDctLines - 1) / kDctLines), kBlock, smem, s>>>(
-            in, out, C, m, 1, rows, inverse ? 1 : 0);
+            in, out, Cp, m, 1, rows, 0);
     } else {
         if (!attr_set[1]) {
             const cudaError_t e =
@@ -1082,7 +1086,8 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const D
             return cudaGetLastError();
         }
         const dim3 grid((unsigned)((inner + kDctLines - 1) / kDctLines), (unsigned)outer);
-        dct_tile_kernel<false><<<grid, kBlock, smem, s>>>(in, out, C, m, inner, inner * m * outer, inverse ? 1 : 0);
+        const int vec_in = (inner % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0) ? 1 : 0;
+        dct_tile_kernel<false><<<grid, kBlock, smem, s>>>(in, out, Cp, m, inner, inner * m * outer, vec_in);
     }
     return cudaGetLastError();
 }

@@ -140,7 +140,10 @@ cudaError_t launch_divergence(int d, const float* x, float* div, const DevGrid& 
 // out_c = addsrc + smu * A x_c + slm * D_c^T div + gamma * x_c (elastic operator)
 cudaError_t launch_elastic(int d, const float* x, const float* div, float* out, const DevGrid& g, int K,
                            float smu, float slm, float gamma, const float* addsrc, cudaStream_t s);
-cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const DevGrid& g, int d,
+// one axis of the spectral transform: C the m x m matrix (untiled kernel,
+// axes of more than 128 cells), Cp its padded table of the direction (Cf
+// forward, Ci inverse; tiled kernel)
+cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const float* Cp, const DevGrid& g, int d,
                             int nblocks_kd, int axis, bool inverse, cudaStream_t s);
 // Padded DCT tables per axis (rows of P = m rounded up to 4 floats, zero past
 // m): forward Cf[q][k] = C[k][q], inverse Ci[q][k] = C[q][k].

@@ -1020,19 +1020,45 @@ __device__ __forceinline__ void ell_scatter(const EllArgs& A, long long key, con
         red_vec(G + corner_elem<D>(A.vg, (size_t)key, 0, c & 1, (c >> 1) & 1, (c >> 2) & 1), b + c * D, w);
 }
 
+// Scatter of the first blocks of a warp's rows with neighbouring rows paired:
+// voxels next to each other in x mostly trace through the same velocity cell,
+// so a run of lanes with equal keys adds its weighted blocks two by two through
+// shuffles before the reductions, and only the lane at an even position of the
+// run reduces (about half the global reductions).  Every lane of the warp calls
+// it; lanes without a block pass a key no other lane has.
+template <int D>
+__device__ __forceinline__ void ell_scatter_paired(const EllArgs& A, long long key, const float* b, float w) {
+    constexpr int B = (1 << D) * D;
+    const int lane = threadIdx.x & 31;
+    const long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const long long next = __shfl_down_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // the run's first lane
+    const bool absorbed = ((lane - start) & 1) != 0;
+    const bool absorber = !absorbed && lane < 31 && next == key;
+    float wb[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        wb[k] = w * b[k];
+        const float o = __shfl_down_sync(0xffffffffu, wb[k], 1);
+        if (absorber) wb[k] += o;
+    }
+    if (!absorbed && key >= 0) ell_scatter<D>(A, key, wb, 1.0f);
+}
+
 template <int D, int EMODE>
 __global__ void __launch_bounds__(kEllBlock) ell_kernel(const EllArgs A) {
     constexpr int B = (1 << D) * D;
     constexpr int RB = kEllRegBlocks;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.M) return;
+    const bool valid = i < A.M;           // lanes past the end stay for the warp's shuffles
     const float* dV = static_cast<const float*>(A.dV);
-    const int n = __ldg(A.ecnt + i);
+    const int n = valid ? __ldg(A.ecnt + i) : 0;
     long long kr[RB > 0 ? RB : 1];
     float br[RB > 0 ? RB : 1][B];
 #pragma unroll
     for (int j = 0; j < RB; ++j)
-        if (j == 0 || j < n) ell_load<D>(A, i, j, kr[j], br[j]);
+        if (valid && (j == 0 || j < n)) ell_load<D>(A, i, j, kr[j], br[j]);
     float s = 0.0f;
     if (EMODE != ELL_JTVP) {
 #pragma unroll
@@ -1046,15 +1072,17 @@ __global__ void __launch_bounds__(kEllBlock) ell_kernel(const EllArgs A) {
             s += ell_dot<D>(A, dV, k, b);
         }
         if (EMODE == ELL_JVP) {
-            A.out[i] = s;
+            if (valid) A.out[i] = s;
             return;
         }
         s *= A.cellvol;
     } else {
-        s = A.r[i];
+        s = valid ? A.r[i] : 0.0f;
     }
+    // the first block: paired across the warp; keys are non-negative element offsets
+    ell_scatter_paired<D>(A, n > 0 ? kr[0] : -1 - (long long)(threadIdx.x & 31), br[0], s);
 #pragma unroll
-    for (int j = 0; j < RB; ++j)
+    for (int j = 1; j < RB; ++j)
         if (j < n) ell_scatter<D>(A, kr[j], br[j], s);
 #pragma unroll 1
     for (int j = RB; j < n; ++j) {
