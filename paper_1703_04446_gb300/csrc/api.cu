@@ -404,7 +404,9 @@ lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, cons
 }
 
 // out = J^T h^d J dv + alpha dt h_v^d A dv + gamma dv at the packed velocity.
-lgnk_status hessvec_packed(lgnk_ctx* ctx, const float* T, const float* dv, float* out) {
+// The data term of the Gauss-Newton product into the slice gradients Gp
+// (the first half of hessvec_packed).
+lgnk_status hessvec_accumulate(lgnk_ctx* ctx, const float* T, const float* dv) {
     TRY(pack_v(ctx, dv, ctx->dVp));
     TRY(zero_G(ctx));
     if (ctx->prob.model == LGNK_TRANSPORT) {
@@ -422,8 +424,18 @@ lgnk_status hessvec_packed(lgnk_ctx* ctx, const float* T, const float* dv, float
         b.r = ctx->acc;
         TRY(trace(ctx, MODE_JTVP, b));
     }
+    return LGNK_OK;
+}
+
+// out = the distributed slice gradients + the regularizer's term of dv.
+lgnk_status hessvec_finish(lgnk_ctx* ctx, const float* dv, float* out) {
     KL(launch_distribute_gradient(ctx->d, ctx->Gp, out, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
     return reg_apply(ctx, dv, out, ctx->prob.alpha * ctx->wreg, ctx->prob.gamma, out);
+}
+
+lgnk_status hessvec_packed(lgnk_ctx* ctx, const float* T, const float* dv, float* out) {
+    TRY(hessvec_accumulate(ctx, T, dv));
+    return hessvec_finish(ctx, dv, out);
 }
 
 EllArgs ell_args(const lgnk_ctx* ctx) {
@@ -519,12 +531,15 @@ lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float
     return LGNK_OK;
 }
 
-lgnk_status hessvec_assembled_packed(lgnk_ctx* ctx, const float* dv, float* out) {
+lgnk_status hessvec_assembled_accumulate(lgnk_ctx* ctx, const float* dv) {
     TRY(pack_v(ctx, dv, ctx->dVp));
     TRY(zero_G(ctx));
-    TRY(ell(ctx, ELL_HESS, ell_args(ctx)));
-    KL(launch_distribute_gradient(ctx->d, ctx->Gp, out, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
-    return reg_apply(ctx, dv, out, ctx->prob.alpha * ctx->wreg, ctx->prob.gamma, out);
+    return ell(ctx, ELL_HESS, ell_args(ctx));
+}
+
+lgnk_status hessvec_assembled_packed(lgnk_ctx* ctx, const float* dv, float* out) {
+    TRY(hessvec_assembled_accumulate(ctx, dv));
+    return hessvec_finish(ctx, dv, out);
 }
 
 lgnk_status precond_apply(lgnk_ctx* ctx, const float* r, float* z) {
@@ -1069,11 +1084,20 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
         // CUDA graphs need a capturable stream and no per-launch profiling events
         const bool use_graphs = !ctx->prof && s == ctx->solve_stream && s != nullptr;
         // the device work of one iteration; ends with p.Hp and r.r in hres[2], hres[3]
+        // with the diffusion regularizer, the end of the product, p.Hp and alpha are one kernel
+        const bool fused_finish = ctx->prob.regularizer == LGNK_DIFFUSION;
         auto body = [&](bool readback) -> lgnk_status {
-            TRY(use_asm ? hessvec_assembled_packed(ctx, p, Hp) : hessvec_packed(ctx, T, p, Hp));
-            KL(launch_dot_fused(p, Hp, nullptr, n, ctx->partial, nb, ctx->dcounter, ctx->dres, 2, 2, 0, ctx->fsc, s));
-            KL(launch_axpby_dev(0.0f, ctx->fsc + 0, p, 1.0f, nullptr, x, n, s));
-            KL(launch_axpby_dev(0.0f, ctx->fsc + 1, Hp, 1.0f, nullptr, r, n, s));
+            TRY(use_asm ? hessvec_assembled_accumulate(ctx, p) : hessvec_accumulate(ctx, T, p));
+            if (fused_finish) {
+                KL(launch_hess_finish(ctx->d, ctx->Gp, p, Hp, ctx->vg, ctx->K, ctx->slices, 1.0f,
+                                      (float)(ctx->prob.alpha * ctx->wreg), (float)ctx->prob.gamma, ctx->partial, nb,
+                                      ctx->dcounter, ctx->dres, ctx->fsc, s));
+            } else {
+                TRY(hessvec_finish(ctx, p, Hp));
+                KL(launch_dot_fused(p, Hp, nullptr, n, ctx->partial, nb, ctx->dcounter, ctx->dres, 2, 2, 0, ctx->fsc,
+                                    s));
+            }
+            KL(launch_pcg_update_xr(x, p, r, Hp, ctx->fsc, n, s));
             if (o.precond) TRY(precond_apply(ctx, r, z));
             else CK(cudaMemcpyAsync(z, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
             KL(launch_dot_fused(r, r, z, n, ctx->partial, nb, ctx->dcounter, ctx->dres, 3, 4, 1, ctx->fsc, s));

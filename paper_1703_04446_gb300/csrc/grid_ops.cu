@@ -69,6 +69,14 @@ __global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restr
     }
 }
 
+// Cell coordinates of node s of an (unpadded) velocity block.
+template <int D>
+__device__ __forceinline__ void coords(size_t s, const DevGrid& g, int* c) {
+    c[0] = (int)(s % g.m[0]);
+    c[1] = (int)((s / g.m[0]) % g.m[1]);
+    c[2] = (D == 3) ? (int)(s / ((size_t)g.m[0] * g.m[1])) : 0;
+}
+
 // Adjoint of the slice packing for the gradient: node j of component c gets
 // scale * sum_m w_j(m) G_m[node], w_j(m) = 1 - th[m] if j = j[m], th[m] if j = j[m] + 1.
 template <int D>
@@ -206,17 +214,14 @@ __device__ __forceinline__ void pcg_step_lengths(double* sc, float* f, int mode)
     }
 }
 
-__global__ void dot_fused_kernel(const float* __restrict__ a, const float* __restrict__ b,
-                                 const float* __restrict__ c, size_t count, double* partial, unsigned* counter,
-                                 double* sc, int slot_b, int slot_c, int mode, float* f) {
-    fpair s = fpair_zero(), t = fpair_zero();
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const float ai = a[i];
-        fpair_add_prod(s, ai, b[i]);
-        if (c != nullptr) fpair_add_prod(t, ai, c[i]);
-    }
+// Second half of the fused inner products: block sums of the per-thread pairs
+// s (a.b) and, when `two`, t (a.c); every block writes its partials and the
+// last block to finish adds them in a fixed order into sc[slot_b] (sc[slot_c])
+// and applies pcg_step_lengths(mode).  Every thread of every block calls it.
+__device__ __forceinline__ void dot_blocks_finish(fpair s, fpair t, bool two, double* partial, unsigned* counter,
+                                                  double* sc, int slot_b, int slot_c, int mode, float* f) {
     s = fpair_block_sum(s);
-    if (c != nullptr) {
+    if (two) {
         __syncthreads();      // fpair_block_sum's shared slots are reused
         t = fpair_block_sum(t);
     }
@@ -225,7 +230,7 @@ __global__ void dot_fused_kernel(const float* __restrict__ a, const float* __res
     if (threadIdx.x == 0) {
         pp[2 * blockIdx.x] = s.hi;
         pp[2 * blockIdx.x + 1] = s.lo;
-        if (c != nullptr) {
+        if (two) {
             pp[2 * (gridDim.x + blockIdx.x)] = t.hi;
             pp[2 * (gridDim.x + blockIdx.x) + 1] = t.lo;
         }
@@ -239,19 +244,101 @@ __global__ void dot_fused_kernel(const float* __restrict__ a, const float* __res
     fpair u = fpair_zero(), w = fpair_zero();
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         fpair_add(u, fpair{vp[2 * i], vp[2 * i + 1]});
-        if (c != nullptr) fpair_add(w, fpair{vp[2 * (gridDim.x + i)], vp[2 * (gridDim.x + i) + 1]});
+        if (two) fpair_add(w, fpair{vp[2 * (gridDim.x + i)], vp[2 * (gridDim.x + i) + 1]});
     }
-    __syncthreads();          // the first phase's fpair_block_sum slots are reused
+    __syncthreads();          // the first block sums' shared slots are reused
     u = fpair_block_sum(u);
-    if (c != nullptr) {
+    if (two) {
         __syncthreads();
         w = fpair_block_sum(w);
     }
     if (threadIdx.x == 0) {
         sc[slot_b] = fpair_value(u);
-        if (c != nullptr) sc[slot_c] = fpair_value(w);
+        if (two) sc[slot_c] = fpair_value(w);
         pcg_step_lengths(sc, f, mode);
         *counter = 0u;
+    }
+}
+
+__global__ void dot_fused_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                 const float* __restrict__ c, size_t count, double* partial, unsigned* counter,
+                                 double* sc, int slot_b, int slot_c, int mode, float* f) {
+    fpair s = fpair_zero(), t = fpair_zero();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const float ai = a[i];
+        fpair_add_prod(s, ai, b[i]);
+        if (c != nullptr) fpair_add_prod(t, ai, c[i]);
+    }
+    dot_blocks_finish(s, t, c != nullptr, partial, counter, sc, slot_b, slot_c, mode, f);
+}
+
+// The end of a Gauss-Newton product inside PCG with the diffusion
+// regularizer, in one pass over the velocity nodes: Hp = gscale * (slice
+// gradients distributed to the time nodes) + rscale * (B^T B p) + gamma * p
+// (the arithmetic of distribute_gradient_kernel and laplacian_kernel, in the
+// same order), then p.Hp into sc[2] and the step length alpha (mode 0), as
+// dot_fused_kernel does.  Launched with the same block count as the fused
+// inner products (partial holds one pair per block).
+template <int D>
+__global__ void hess_finish_kernel(const float* __restrict__ Gp, const float* __restrict__ p, float* __restrict__ Hp,
+                                   DevGrid g, int K, SliceTable tab, float gscale, float rscale, float gamma,
+                                   double* partial, unsigned* counter, double* sc, float* f) {
+    const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
+    const size_t nodes = padded_size(g);
+    const size_t total = Mv * K;
+    const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
+    fpair dsum = fpair_zero();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t sn = i % Mv;
+        const int j = (int)(i / Mv);
+        int c[3];
+        coords<D>(sn, g, c);
+        const size_t node =
+            ((size_t)(c[2] + (D == 3 ? LGNK_PAD : 0)) * g.mp[1] + (c[1] + LGNK_PAD)) * g.mp[0] + (c[0] + LGNK_PAD);
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int m = 0; m < tab.n; ++m) {
+            float w = 0.0f;
+            if (tab.j[m] == j) w = 1.0f - tab.th[m];
+            else if (tab.j[m] + 1 == j) w = tab.th[m];
+            if (w == 0.0f) continue;
+            const size_t e = (size_t)m * nodes + node;
+            if (D == 3) {
+                const float4 a = reinterpret_cast<const float4*>(Gp)[e];
+                acc[0] = fmaf(w, a.x, acc[0]); acc[1] = fmaf(w, a.y, acc[1]); acc[2] = fmaf(w, a.z, acc[2]);
+            } else {
+                const float2 a = reinterpret_cast<const float2*>(Gp)[e];
+                acc[0] = fmaf(w, a.x, acc[0]); acc[1] = fmaf(w, a.y, acc[1]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const size_t k = ((size_t)j * D + q) * Mv + sn;
+            const float xi = p[k];
+            float lap = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                float t = 0.0f;
+                if (c[a] > 0) t += xi - p[k - stride[a]];
+                if (c[a] < g.m[a] - 1) t += xi - p[k + stride[a]];
+                lap = fmaf(t, g.inv_h[a] * g.inv_h[a], lap);
+            }
+            float r = rscale * lap;
+            if (gamma != 0.0f) r = fmaf(gamma, xi, r);
+            r += gscale * acc[q];
+            Hp[k] = r;
+            fpair_add_prod(dsum, xi, r);
+        }
+    }
+    dot_blocks_finish(dsum, fpair_zero(), false, partial, counter, sc, 2, 2, 0, f);
+}
+
+// x += f[0] p and r += f[1] Hp (the PCG updates with alpha, -alpha)
+__global__ void pcg_update_xr_kernel(float* x, const float* __restrict__ p, float* r, const float* __restrict__ Hp,
+                                     const float* __restrict__ f, size_t count) {
+    const float a = f[0], b = f[1];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        x[i] = fmaf(a, p[i], x[i]);
+        r[i] = fmaf(b, Hp[i], r[i]);
     }
 }
 
@@ -294,13 +381,6 @@ __global__ void reduce_kernel(const double* __restrict__ partial, int count, dou
 }
 
 // ----------------------------------------------------------- regularizers --
-
-template <int D>
-__device__ __forceinline__ void coords(size_t s, const DevGrid& g, int* c) {
-    c[0] = (int)(s % g.m[0]);
-    c[1] = (int)((s / g.m[0]) % g.m[1]);
-    c[2] = (D == 3) ? (int)(s / ((size_t)g.m[0] * g.m[1])) : 0;
-}
 
 // out = addsrc + scale * (B^T B x) + gamma * gsrc: the Neumann Laplacian of each
 // (time node, component) block, B the forward difference between neighbouring
@@ -995,6 +1075,24 @@ cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, siz
                              int nblocks, unsigned* counter, double* sc, int slot_b, int slot_c, int mode, float* f,
                              cudaStream_t s) {
     dot_fused_kernel<<<nblocks, kBlock, 0, s>>>(a, b, c, count, partial, counter, sc, slot_b, slot_c, mode, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hess_finish(int d, const void* Gp, const float* p, float* Hp, const DevGrid& g, int K,
+                               const SliceTable& t, float gscale, float rscale, float gamma, double* partial,
+                               int nblocks, unsigned* counter, double* sc, float* f, cudaStream_t s) {
+    if (d == 3)
+        hess_finish_kernel<3><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale, rscale, gamma,
+                                                         partial, counter, sc, f);
+    else
+        hess_finish_kernel<2><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale, rscale, gamma,
+                                                         partial, counter, sc, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update_xr(float* x, const float* p, float* r, const float* Hp, const float* f, size_t count,
+                                 cudaStream_t s) {
+    pcg_update_xr_kernel<<<grid_for(count), kBlock, 0, s>>>(x, p, r, Hp, f, count);
     return cudaGetLastError();
 }
 

@@ -124,6 +124,14 @@ int dot_blocks(size_t count);
 cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, size_t count, double* partial,
                              int nblocks, unsigned* counter, double* sc, int slot_b, int slot_c, int mode, float* f,
                              cudaStream_t s);
+// Hp = gscale * distributed slice gradients + rscale * B^T B p + gamma * p (diffusion
+// regularizer), then p.Hp into sc[2] and alpha (fused inner-product step, mode 0)
+cudaError_t launch_hess_finish(int d, const void* Gp, const float* p, float* Hp, const DevGrid& g, int K,
+                               const SliceTable& t, float gscale, float rscale, float gamma, double* partial,
+                               int nblocks, unsigned* counter, double* sc, float* f, cudaStream_t s);
+// x += f[0] p, r += f[1] Hp
+cudaError_t launch_pcg_update_xr(float* x, const float* p, float* r, const float* Hp, const float* f, size_t count,
+                                 cudaStream_t s);
 // PCG loop test at the end of an iteration of a device-side while loop (see grid_ops.cu)
 cudaError_t launch_pcg_control(const double* sc, int* ctl, cudaGraphConditionalHandle handle, cudaStream_t s);
 cudaError_t launch_axpby_dev(float a, const float* ap, const float* x, float b, const float* bp, float* y,
