@@ -194,7 +194,7 @@ def fp32_peak_tflops():
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for name in ("trace_impl.cuh", "trace3d.cu", "lgnk_internal.h"):
+    for name in ("trace_impl.cuh", "fsum.cuh", "trace3d.cu", "lgnk_internal.h"):
         with open(os.path.join(ROOT, "paper_1703_04446_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -585,8 +585,10 @@ def profile_case(args):
             cctx.hessvec(cv, rho, cdv, cout)
         out = cout
     elif args.profile_case == "solve":
-        # `launches` Gauss-Newton iterations from v = 0 towards the phantom moved by v
+        # `launches` Gauss-Newton iterations from v = 0 towards the phantom moved by v, with
+        # direct launches (profiling mode: no CUDA graphs) so that a profiler sees every PCG kernel
         R = ctx.forward(tv, tT)
+        ctx.profile(True)
         _, rep = ctx.solve(tT, R, None, max_gn=args.launches, gn_grad_rtol=1e-3, max_pcg=50, pcg_rtol=0.1)
         out.copy_(tdv)
         print(json.dumps({k: rep[k] for k in ("gn_iters", "pcg_iters", "hessvecs", "seconds")}))
