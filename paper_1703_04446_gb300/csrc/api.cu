@@ -407,8 +407,8 @@ lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, cons
 // The data term of the Gauss-Newton product into the slice gradients Gp
 // (the first half of hessvec_packed).
 lgnk_status hessvec_accumulate(lgnk_ctx* ctx, const float* T, const float* dv) {
-    TRY(pack_v(ctx, dv, ctx->dVp));
-    TRY(zero_G(ctx));
+    // packs the direction and zeroes the slice gradients in one pass
+    KL(launch_pack_velocity(ctx->d, dv, ctx->dVp, ctx->vg, ctx->K, ctx->slices, ctx->stream, ctx->Gp));
     if (ctx->prob.model == LGNK_TRANSPORT) {
         TraceArgs a = base_args(ctx);
         TRY(trace(ctx, MODE_HESS, a));
@@ -532,8 +532,7 @@ lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float
 }
 
 lgnk_status hessvec_assembled_accumulate(lgnk_ctx* ctx, const float* dv) {
-    TRY(pack_v(ctx, dv, ctx->dVp));
-    TRY(zero_G(ctx));
+    KL(launch_pack_velocity(ctx->d, dv, ctx->dVp, ctx->vg, ctx->K, ctx->slices, ctx->stream, ctx->Gp));
     return ell(ctx, ELL_HESS, ell_args(ctx));
 }
 

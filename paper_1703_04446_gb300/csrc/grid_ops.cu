@@ -29,14 +29,20 @@ __device__ __forceinline__ size_t padded_size(const DevGrid& g) {
 // t_m (linear in time between the K nodes) at the padded node and at its +x
 // neighbour, [v(node) | v(node + 1)], as 8 floats (3D: xyz + zero pad, twice;
 // 32 bytes) or 4 floats (2D).  One 256-bit (3D) or 128-bit (2D) load then
-// returns both x-corners of a cell row.
+// returns both x-corners of a cell row.  With Gz given, the slice gradients,
+// which share the [slice][padded node] index, are zeroed in the same pass.
 template <int D>
-__global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restrict__ Vp, DevGrid g, SliceTable tab) {
+__global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restrict__ Vp, DevGrid g, SliceTable tab,
+                                     void* Gz) {
     const size_t nodes = padded_size(g);
     const size_t total = nodes * tab.n;
     const size_t Mv = (size_t)g.m[0] * g.m[1] * g.m[2];
     constexpr int PS = (D == 3) ? 8 : 4;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        if (Gz != nullptr) {
+            if (D == 3) reinterpret_cast<float4*>(Gz)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            else reinterpret_cast<float2*>(Gz)[i] = make_float2(0.0f, 0.0f);
+        }
         const int m = (int)(i / nodes);
         const size_t node = i % nodes;
         const int j = tab.j[m];
@@ -995,11 +1001,11 @@ inline int grid_for(size_t count) {
 }  // namespace
 
 cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, const SliceTable& t,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, void* Gz) {
     (void)K;
     const size_t total = (size_t)g.mp[0] * g.mp[1] * g.mp[2] * t.n;
-    if (d == 3) pack_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, t);
-    else pack_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, t);
+    if (d == 3) pack_velocity_kernel<3><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, t, Gz);
+    else pack_velocity_kernel<2><<<grid_for(total), kBlock, 0, s>>>(v, (float*)Vp, g, t, Gz);
     return cudaGetLastError();
 }
 

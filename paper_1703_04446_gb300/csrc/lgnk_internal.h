@@ -101,8 +101,9 @@ cudaError_t launch_trace(int d, bool nonstat, int model, int mode, const TraceAr
 // grid utilities (grid_ops.cu)
 // ABI velocity [K][d][z][y][x] -> pair-packed padded time slices
 // (velocity_pair_bytes(d) bytes per node and slice)
+// (and, when Gz is given, zero the slice gradients of the same slices and padding)
 cudaError_t launch_pack_velocity(int d, const float* v, void* Vp, const DevGrid& g, int K, const SliceTable& t,
-                                 cudaStream_t s);
+                                 cudaStream_t s, void* Gz = nullptr);
 inline size_t velocity_pair_bytes(int d) { return d == 3 ? 32 : 16; }
 // slice gradients [m][padded nodes] -> ABI [K][d][z][y][x], out = scale * sum_m w_j(m) G_m
 cudaError_t launch_distribute_gradient(int d, const void* Gp, float* out, const DevGrid& g, int K,
