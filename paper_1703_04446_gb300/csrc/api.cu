@@ -26,6 +26,54 @@ cudaError_t launch_ell(int d, int mode, const EllArgs& a, cudaStream_t s) {
     return d == 3 ? launch_ell_3d(mode, a, s) : launch_ell_2d(mode, a, s);
 }
 
+// One PCG iteration's device work as a replayable CUDA graph (one per
+// matvec variant), kept in the context across solves.  Captured on first
+// use; the launches it holds are counted on every replay.  Everything the
+// capture holds is fixed for the context (the solver's vectors and buffers,
+// the problem's constants) except what the key records: whether the
+// preconditioner is applied, and the template pointer (taken by the
+// matrix-free mass-preserving product).
+struct PcgGraphKey {
+    int precond = -1;
+    const float* T = nullptr;
+    bool operator==(const PcgGraphKey& o) const { return precond == o.precond && T == o.T; }
+};
+
+struct PcgGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0, trace_launches = 0;
+    bool failed = false;
+    PcgGraphKey key;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        launches = trace_launches = 0;
+        failed = false;
+    }
+    ~PcgGraph() { reset(); }
+};
+
+// The whole PCG loop of one GN step as one graph: a while node whose body is
+// one iteration followed by launch_pcg_control, which ends the loop on the
+// stopping test, non-positive curvature or the iteration cap.  The host reads
+// the loop state once per GN step instead of once per iteration.
+struct PcgLoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0, trace_launches = 0;   // per iteration
+    bool failed = false;
+    PcgGraphKey key;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        launches = trace_launches = 0;
+        failed = false;
+    }
+    ~PcgLoopGraph() { reset(); }
+};
+
 struct lgnk_ctx {
     lgnk_problem prob;
     cudaStream_t stream = nullptr;
@@ -47,6 +95,8 @@ struct lgnk_ctx {
     // the DCT matrices in the shared-memory layouts of the tiled kernels, rows
     // padded to P = m rounded up to 4: forward Cf[q][k] = C[k][q], inverse Ci[q][k] = C[q][k]
     float *Cf[3] = {nullptr, nullptr, nullptr}, *Ci[3] = {nullptr, nullptr, nullptr};
+    PcgGraph pcg_graphs[2];       // [0] matrix-free, [1] assembled products
+    PcgLoopGraph pcg_loops[2];
     double* partial = nullptr;
     double* cpartial = nullptr;   // per-block entry counts of the assembled rows
     int npartial = 0;
@@ -640,6 +690,10 @@ size_t lgnk_scratch_bytes(const lgnk_ctx* ctx) {
 
 void lgnk_destroy(lgnk_ctx* ctx) {
     if (ctx == nullptr) return;
+    for (int i = 0; i < 2; ++i) {   // before the stream and the buffers they use
+        ctx->pcg_loops[i].reset();
+        ctx->pcg_graphs[i].reset();
+    }
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->ev_enter) cudaEventDestroy(ctx->ev_enter);
     if (ctx->ev_leave) cudaEventDestroy(ctx->ev_leave);
@@ -987,33 +1041,6 @@ void lgnk_solve_opts_default(lgnk_solve_opts* o) {
     o->matvec = 1;
 }
 
-// One PCG iteration's device work as a replayable CUDA graph (one per
-// matvec variant and solve).  Captured on first use; the launches it holds
-// are counted on every replay.
-struct PcgGraph {
-    cudaGraphExec_t exec = nullptr;
-    long long launches = 0, trace_launches = 0;
-    bool failed = false;
-    ~PcgGraph() {
-        if (exec) cudaGraphExecDestroy(exec);
-    }
-};
-
-// The whole PCG loop of one GN step as one graph: a while node whose body is
-// one iteration followed by launch_pcg_control, which ends the loop on the
-// stopping test, non-positive curvature or the iteration cap.  The host reads
-// the loop state once per GN step instead of once per iteration.
-struct PcgLoopGraph {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    long long launches = 0, trace_launches = 0;   // per iteration
-    bool failed = false;
-    ~PcgLoopGraph() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-    }
-};
-
 lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, const lgnk_solve_opts& o,
                        lgnk_solve_report* rep_out) {
     const auto t_start = std::chrono::steady_clock::now();
@@ -1025,8 +1052,6 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
           *vt = ctx->sv[6];
     const size_t n = ctx->n;
     cudaStream_t s = ctx->stream;
-    PcgGraph graphs[2];           // [0] matrix-free, [1] assembled
-    PcgLoopGraph loops[2];
     lgnk_solve_report rep;
     memset(&rep, 0, sizeof(rep));
 
@@ -1104,8 +1129,19 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             if (readback) CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
             return LGNK_OK;
         };
-        PcgGraph& gr = graphs[use_asm ? 1 : 0];
-        PcgLoopGraph& lg = loops[use_asm ? 1 : 0];
+        PcgGraph& gr = ctx->pcg_graphs[use_asm ? 1 : 0];
+        PcgLoopGraph& lg = ctx->pcg_loops[use_asm ? 1 : 0];
+        PcgGraphKey key;
+        key.precond = o.precond ? 1 : 0;
+        key.T = use_asm ? nullptr : T;
+        if (!(lg.key == key)) {
+            lg.reset();
+            lg.key = key;
+        }
+        if (!(gr.key == key)) {
+            gr.reset();
+            gr.key = key;
+        }
         int pit = 0;
         if (use_graphs && lg.exec == nullptr && !lg.failed) {
             // build the loop graph; any failure falls back to one graph per iteration
