@@ -120,7 +120,9 @@ lgnk_status lgnk_jtvp(lgnk_ctx* ctx, const float* v, const float* T, const float
  * S = 1/2 dt h_v^d |B v|^2 (dt = 1/(K-1), 1 when stationary).  J, D, S: host
  * doubles (each may be NULL).  grad: NULL or device [n] receiving
  * d_v J = (d_v u1)^T h^d (u1 - R) + alpha dt h_v^d B^T B v (Sec. 3.2).
- * Sums are accumulated in FP64.  Synchronises the stream. */
+ * Sums are accumulated in pairs of FP32 values with exact rounding errors
+ * (about 48 significant bits) and combined per block in FP64.  Synchronises
+ * the stream. */
 lgnk_status lgnk_objective(lgnk_ctx* ctx, const float* v, const float* T, const float* R,
                            double* J, double* D, double* S, float* grad);
 
@@ -261,7 +263,8 @@ lgnk_status lgnk_solve_multilevel(const lgnk_problem* fine, int levels, void* st
  *
  * prob: validated as in lgnk_create; model must be LGNK_TRANSPORT.
  * v[n], T[M] in; u1[M] out (device).  R[M] (device) and D (device, one double)
- * are both NULL or both given: D = h^d/2 |u1 - R|^2, summed in FP64.
+ * are both NULL or both given: D = h^d/2 |u1 - R|^2, summed in FP32 pairs (about
+ * 48 bits) and per block in FP64.
  * stream: cudaStream_t (NULL = legacy default stream); the call only enqueues.
  *
  * Scratch: a file-scope device array of 32 MiB (every GPU that loads the

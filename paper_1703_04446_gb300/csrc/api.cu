@@ -1,7 +1,7 @@
 // C ABI of the lgnk library (declared in include/lgnk.h): context and scratch
 // management, the hot-path entry points, and the host-driven inexact
-// Gauss-Newton-Krylov loop (Eq. 11) whose vector work and FP64 inner products
-// run on the device.
+// Gauss-Newton-Krylov loop (Eq. 11) whose vector work and inner products run
+// on the device.
 #include <chrono>
 #include <cmath>
 #include <cstdio>

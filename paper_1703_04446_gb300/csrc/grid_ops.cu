@@ -204,8 +204,9 @@ __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict_
 // launch: every block writes its partial sums (FP32 pairs, stored in the FP64
 // partial buffer's slots), and the last block to finish (a counter, reset by
 // that block) adds the partials in a fixed order (deterministic) into
-// sc[slot_b] (a.b) and sc[slot_c] (a.c, when c is given), then the PCG step lengths of step `mode` (-1: none) from the FP64
-// inner products in sc ([2] p.Hp, [3] r.r, [4] r.z new, [5] r.z current):
+// sc[slot_b] (a.b) and sc[slot_c] (a.c, when c is given), then the PCG step
+// lengths of step `mode` (-1: none), in FP64, from the inner products in sc
+// ([2] p.Hp, [3] r.r, [4] r.z new, [5] r.z current):
 //   mode 0: alpha = rz / pHp, or 0 when pHp is not positive; f[0] = alpha, f[1] = -alpha
 //   mode 1: beta = rz_new / rz, then rz = rz_new;             f[2] = beta
 __device__ __forceinline__ void pcg_step_lengths(double* sc, float* f, int mode) {

@@ -65,7 +65,7 @@ struct TraceArgs {
     float* yout;              // optional end points [d][M]
     float* acc;               // continuity splat accumulator (padded image)
     void* G;                  // gradient accumulator slices [m][zp][yp][xp] of float4 (3D) / float2 (2D)
-    double* partial;          // per-block FP64 partial sums of res^2
+    double* partial;          // per-block partial sums of res^2 (FP32-pair sums, stored in FP64)
     // MODE_ASM (transport): rows of the assembled J, entry-major [e][voxel]
     long long* ekey;          // element of the lower corner of the entry's cell in the slice gradient space
     float* eblk;              // [e][corner][component][voxel]: sum of w_corner * mu over the cell's stages
