@@ -9,7 +9,7 @@ import pytest
 import torch
 
 from oracle import lagrangian as L
-from oracle.objective import hessvec
+from oracle.objective import Problem as OProblem, hessvec
 from paper_1703_04446_gb300 import synth
 from tests._cases import CASES, make_case, rel
 
@@ -111,6 +111,24 @@ def test_capacity_overflow_is_reported_and_the_solver_falls_back():
     assert rep_as["gn_iters"] == rep_mf["gn_iters"]
     # the same solve twice: only the order of float atomics in the gradient scatter differs
     assert abs(rep_as["J"] - rep_mf["J"]) <= 1e-4 * abs(rep_mf["J"])
+
+
+def test_matrix_free_product_where_rows_overflow():
+    """Where the rows of J are too long to assemble (3 time nodes, 12 steps,
+    large displacements), the solver falls back to the matrix-free product:
+    it matches the oracle's Gauss-Newton product on that case."""
+    from paper_1703_04446_gb300 import lgnk
+    ctx, v, T, R = _overflow_case()
+    with pytest.raises(lgnk.LgnkError) as e:
+        ctx.assemble(v, T)               # the rows do not fit: the overflow path is taken
+    assert e.value.status == 8
+    im, vm = (16, 16, 16), (8, 8, 8)
+    op = OProblem(L.Grid(im), L.Grid(vm), K=3, N=12, model="transport")
+    g = synth.GridSpec(vm, (0.0,) * 3, (1.0,) * 3)
+    dv = synth.random_velocity(g, 3, 0.05, 8).astype(np.float32)
+    ref = hessvec(op, _np(v), _np(T), dv.astype(np.float64))
+    got = _np(ctx.hessvec(v, T, torch.from_numpy(dv).cuda()))
+    assert rel(got, ref) <= TOL
 
 
 def test_solver_with_assembled_matvec_matches_matrix_free():
