@@ -608,6 +608,9 @@ lgnk_status precond_apply(lgnk_ctx* ctx, const float* r, float* z) {
             KL(launch_dct_last_fused(ctx->pc1, ctx->pc0, ctx->Cf[2], ctx->Ci[2], ctx->inv_eig, ctx->vg, 3, kd, s));
             KL(launch_dct_axis(ctx->pc0, ctx->pc1, ctx->Cm[1], ctx->Ci[1], ctx->vg, 3, kd, 1, true, s));
             KL(launch_dct_axis(ctx->pc1, z, ctx->Cm[0], ctx->Ci[0], ctx->vg, 3, kd, 0, true, s));
+        } else if (ctx->d == 2 && ctx->vg.m[0] <= 64 && ctx->vg.m[1] <= 64) {
+            // the whole transform of each plane in one CTA: one launch
+            KL(launch_dct_plane2d(r, z, ctx->Cf[0], ctx->Cf[1], ctx->Ci[0], ctx->Ci[1], ctx->inv_eig, ctx->vg, kd, s));
         } else {
             KL(launch_dct_axis(r, ctx->pc0, ctx->Cm[0], ctx->Cf[0], ctx->vg, 2, kd, 0, false, s));
             KL(launch_dct_last_fused(ctx->pc0, ctx->pc1, ctx->Cf[1], ctx->Ci[1], ctx->inv_eig, ctx->vg, 2, kd, s));

@@ -735,42 +735,17 @@ __global__ void __launch_bounds__(4 * LINES) dct_last_fused_kernel(const float* 
 // commute, so this equals the per-axis passes up to rounding.
 constexpr int kDctPlaneMax = 64;
 
-__global__ void __launch_bounds__(kBlock) dct_plane_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                           const float* __restrict__ Axg,
-                                                           const float* __restrict__ Ayg, int mx, int my,
-                                                           int vec_in, int vec_out) {
-    extern __shared__ __align__(16) float sm[];
-    const int PX = (mx + 3) & ~3, PY = (my + 3) & ~3;
-    const int LS = PX + 4, LT = PY + 4;   // row strides of the plane [y][x] and of the transposed result [x][k]
-    float* Ay = sm;                       // [q][PY]
-    float* Ax = Ay + my * PY;             // [q][PX]
-    float* S = Ax + mx * PX;              // the plane, later the y result transposed
-    const int t = threadIdx.x;
-    for (int e = t; e < my * PY / 4; e += kBlock) cp_async16(Ay + 4 * e, Ayg + 4 * e);
-    for (int e = t; e < mx * PX / 4; e += kBlock) cp_async16(Ax + 4 * e, Axg + 4 * e);
-    const size_t base = (size_t)blockIdx.x * mx * my;
-    if (vec_in) {                         // mx a multiple of 4 (PX = mx), in 16-byte aligned
-        const int c4 = mx / 4;
-        for (int e = t; e < my * c4; e += kBlock) {
-            const int y = e / c4, x = 4 * (e % c4);
-            cp_async16(S + y * LS + x, in + base + (size_t)y * mx + x);
-        }
-    } else {
-        for (int e = t; e < my * PX; e += kBlock) {
-            const int y = e / PX, x = e % PX;
-            S[y * LS + x] = x < mx ? __ldg(in + base + (size_t)y * mx + x) : 0.0f;
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    const int nxb = PX / 4;
-    const bool act = t < (PY / 4) * nxb;  // at most 256 blocks of 4 x 4: one per thread
-    const int kb = act ? t / nxb : 0, xb = act ? t % nxb : 0;
-    float acc[4][4];                      // [k along y][x]
+// The chained products of one plane: the plane is in S as rows [y][LS]; the
+// y product with Ay ([q][PY]) goes back into S transposed, [x][LT], and the x
+// product with Ax ([q][PX]) is left in acc[i][j] = (x index 4 xb + i, y index
+// 4 kb + j) of this thread's block.  Every thread of the CTA calls it (two
+// barriers); act: the thread has a block.
+__device__ __forceinline__ void plane_yx(const float* Ay, const float* Ax, float* S, int mx, int my, int PX, int PY,
+                                         int LS, int LT, bool act, int kb, int xb, float (&acc)[4][4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;   // [k along y][x]
     if (act) {
         const float4* ap = reinterpret_cast<const float4*>(Ay) + kb;
         const float4* sp = reinterpret_cast<const float4*>(S) + xb;
@@ -793,12 +768,11 @@ __global__ void __launch_bounds__(kBlock) dct_plane_kernel(const float* __restri
                 make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
     }
     __syncthreads();
-    if (!act) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;   // now [k along x][y]
-    {
+    if (act) {
         const float4* ap = reinterpret_cast<const float4*>(Ax) + xb;
         const float4* tp = reinterpret_cast<const float4*>(S) + kb;
 #pragma unroll 4
@@ -812,6 +786,29 @@ __global__ void __launch_bounds__(kBlock) dct_plane_kernel(const float* __restri
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
         }
     }
+}
+
+// Stage a plane of `in` (block `plane`) into S rows [y][LS], pad columns zero.
+__device__ __forceinline__ void plane_load(const float* __restrict__ in, size_t base, float* S, int mx, int my, int PX,
+                                           int LS, int vec_in) {
+    const int t = threadIdx.x;
+    if (vec_in) {                         // mx a multiple of 4 (PX = mx), in 16-byte aligned
+        const int c4 = mx / 4;
+        for (int e = t; e < my * c4; e += blockDim.x) {
+            const int y = e / c4, x = 4 * (e % c4);
+            cp_async16(S + y * LS + x, in + base + (size_t)y * mx + x);
+        }
+    } else {
+        for (int e = t; e < my * PX; e += blockDim.x) {
+            const int y = e / PX, x = e % PX;
+            S[y * LS + x] = x < mx ? __ldg(in + base + (size_t)y * mx + x) : 0.0f;
+        }
+    }
+}
+
+// Store this thread's block acc[i][j] = (x 4 xb + i, y 4 kb + j) of the plane.
+__device__ __forceinline__ void plane_store(float* __restrict__ out, size_t base, int mx, int my, int kb, int xb,
+                                            const float (&acc)[4][4], int vec_out) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int y = 4 * kb + j;
@@ -827,10 +824,94 @@ __global__ void __launch_bounds__(kBlock) dct_plane_kernel(const float* __restri
     }
 }
 
-inline size_t dct_plane_smem(int mx, int my) {
+__global__ void __launch_bounds__(kBlock) dct_plane_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                           const float* __restrict__ Axg,
+                                                           const float* __restrict__ Ayg, int mx, int my,
+                                                           int vec_in, int vec_out) {
+    extern __shared__ __align__(16) float sm[];
+    const int PX = (mx + 3) & ~3, PY = (my + 3) & ~3;
+    const int LS = PX + 4, LT = PY + 4;   // row strides of the plane [y][x] and of the transposed result [x][k]
+    float* Ay = sm;                       // [q][PY]
+    float* Ax = Ay + my * PY;             // [q][PX]
+    float* S = Ax + mx * PX;              // the plane, later the y result transposed
+    const int t = threadIdx.x;
+    for (int e = t; e < my * PY / 4; e += kBlock) cp_async16(Ay + 4 * e, Ayg + 4 * e);
+    for (int e = t; e < mx * PX / 4; e += kBlock) cp_async16(Ax + 4 * e, Axg + 4 * e);
+    const size_t base = (size_t)blockIdx.x * mx * my;
+    plane_load(in, base, S, mx, my, PX, LS, vec_in);
+    cp_async_wait_all();
+    __syncthreads();
+    const int nxb = PX / 4;
+    const bool act = t < (PY / 4) * nxb;  // at most 256 blocks of 4 x 4: one per thread
+    const int kb = act ? t / nxb : 0, xb = act ? t % nxb : 0;
+    float acc[4][4];
+    plane_yx(Ay, Ax, S, mx, my, PX, PY, LS, LT, act, kb, xb, acc);
+    if (act) plane_store(out, base, mx, my, kb, xb, acc, vec_out);
+}
+
+// The whole 2D preconditioner on one plane (a (time node, component) block of
+// at most 64 x 64 cells) in one CTA: modes = C_y X C_x^T, scaled by inv_eig,
+// then X = C_y^T modes C_x, with the scaled modes written back into the plane
+// buffer between the two halves.
+__global__ void __launch_bounds__(kBlock) dct_plane2d_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                             const float* __restrict__ Cfx,
+                                                             const float* __restrict__ Cfy,
+                                                             const float* __restrict__ Cix,
+                                                             const float* __restrict__ Ciy,
+                                                             const float* __restrict__ inv_eig, int mx, int my,
+                                                             int vec_in, int vec_out) {
+    extern __shared__ __align__(16) float sm[];
+    const int PX = (mx + 3) & ~3, PY = (my + 3) & ~3;
+    const int LS = PX + 4, LT = PY + 4;
+    float* Fy = sm;                       // forward tables [q][P]
+    float* Fx = Fy + my * PY;
+    float* Iy = Fx + mx * PX;             // inverse tables [q][P]
+    float* Ix = Iy + my * PY;
+    float* S = Ix + mx * PX;
+    const int t = threadIdx.x;
+    for (int e = t; e < my * PY / 4; e += kBlock) {
+        cp_async16(Fy + 4 * e, Cfy + 4 * e);
+        cp_async16(Iy + 4 * e, Ciy + 4 * e);
+    }
+    for (int e = t; e < mx * PX / 4; e += kBlock) {
+        cp_async16(Fx + 4 * e, Cfx + 4 * e);
+        cp_async16(Ix + 4 * e, Cix + 4 * e);
+    }
+    const size_t base = (size_t)blockIdx.x * mx * my;
+    plane_load(in, base, S, mx, my, PX, LS, vec_in);
+    cp_async_wait_all();
+    __syncthreads();
+    const int nxb = PX / 4;
+    const bool act = t < (PY / 4) * nxb;
+    const int kb = act ? t / nxb : 0, xb = act ? t % nxb : 0;
+    float acc[4][4];
+    plane_yx(Fy, Fx, S, mx, my, PX, PY, LS, LT, act, kb, xb, acc);
+    // scale the modes (kx = 4 xb + i, ky = 4 kb + j; padding modes are zero) and put
+    // them back as rows [ky][LS] once every thread is done with the transposed buffer
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int ky = 4 * kb + j;
+            float sc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int kx = 4 * xb + i;
+                sc[i] = (kx < mx && ky < my) ? acc[i][j] * __ldg(inv_eig + (size_t)ky * mx + kx) : 0.0f;
+            }
+            // rows ky >= my are never read (the inverse sums over q < my) and may lie past the buffer
+            if (ky < my) *reinterpret_cast<float4*>(S + ky * LS + 4 * xb) = make_float4(sc[0], sc[1], sc[2], sc[3]);
+        }
+    }
+    __syncthreads();
+    plane_yx(Iy, Ix, S, mx, my, PX, PY, LS, LT, act, kb, xb, acc);
+    if (act) plane_store(out, base, mx, my, kb, xb, acc, vec_out);
+}
+
+inline size_t dct_plane_smem(int mx, int my, int tables = 1) {
     const size_t PX = (size_t)((mx + 3) & ~3), PY = (size_t)((my + 3) & ~3);
     const size_t plane = std::max((size_t)my * (PX + 4), PX * (PY + 4));
-    return ((size_t)my * PY + (size_t)mx * PX + plane) * sizeof(float);
+    return (tables * ((size_t)my * PY + (size_t)mx * PX) + plane) * sizeof(float);
 }
 
 // Shared memory of dct_tile_kernel for an axis of m cells (bytes).
@@ -1214,6 +1295,26 @@ cudaError_t launch_dct_plane(const float* in, float* out, const float* Ax, const
     const int vec_out = (mx % 4 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
     dct_plane_kernel<<<(unsigned)planes, kBlock, dct_plane_smem(mx, my), s>>>(in, out, Ax, Ay, mx, my, vec_in,
                                                                               vec_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dct_plane2d(const float* in, float* out, const float* Cfx, const float* Cfy, const float* Cix,
+                               const float* Ciy, const float* inv_eig, const DevGrid& g, int blocks, cudaStream_t s) {
+    const int mx = g.m[0], my = g.m[1];
+    if (mx > kDctPlaneMax || my > kDctPlaneMax || blocks < 1) return cudaErrorNotSupported;
+    static bool attr_set_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set_dev[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(dct_plane2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)dct_plane_smem(kDctPlaneMax, kDctPlaneMax, 2));
+        if (e != cudaSuccess) return e;
+        attr_set_dev[dev] = true;
+    }
+    const int vec_in = (mx % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0) ? 1 : 0;
+    const int vec_out = (mx % 4 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
+    dct_plane2d_kernel<<<(unsigned)blocks, kBlock, dct_plane_smem(mx, my, 2), s>>>(in, out, Cfx, Cfy, Cix, Ciy, inv_eig,
+                                                                                  mx, my, vec_in, vec_out);
     return cudaGetLastError();
 }
 

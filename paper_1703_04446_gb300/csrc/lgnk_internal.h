@@ -162,6 +162,10 @@ cudaError_t launch_dct_axis(const float* in, float* out, const float* C, const f
 // planes (the per-axis kernels cover them).
 cudaError_t launch_dct_plane(const float* in, float* out, const float* Ax, const float* Ay, const DevGrid& g,
                              long long planes, cudaStream_t s);
+// The whole 2D preconditioner (forward transform, inv_eig, inverse) with one CTA
+// per (time node, component) plane of at most 64 x 64 cells.
+cudaError_t launch_dct_plane2d(const float* in, float* out, const float* Cfx, const float* Cfy, const float* Cix,
+                               const float* Ciy, const float* inv_eig, const DevGrid& g, int blocks, cudaStream_t s);
 // forward DCT, scale by inv_eig and inverse DCT along the last axis in one pass
 // (the axis's Cf and Ci); cudaErrorNotSupported when that axis has more than 128 cells
 cudaError_t launch_dct_last_fused(const float* in, float* out, const float* Cf, const float* Ci, const float* inv_eig,

@@ -96,12 +96,14 @@ def test_preconditioner(name):
 
 
 @pytest.mark.parametrize("vm,K", [((130, 20), 2), ((40, 36, 129), 1), ((128, 128), 1), ((64, 64, 64), 1),
-                                  ((64, 61, 33), 2), ((37, 64, 16), 1), ((65, 40, 20), 1)])
+                                  ((64, 61, 33), 2), ((37, 64, 16), 1), ((65, 40, 20), 1),
+                                  ((64, 61), 2), ((6, 64), 1), ((19, 15), 3)])
 def test_preconditioner_axis_lengths(vm, K):
     """Axes of more than 128 cells take the untiled DCT kernel, the others the
     shared-memory tile (128 is the largest tiled length); 3D xy planes of at
     most 64 x 64 cells take the plane kernel (float4 stores when x is a
-    multiple of 4, scalar ones otherwise), wider ones the per-axis tiles."""
+    multiple of 4, scalar ones otherwise), wider ones the per-axis tiles; 2D
+    planes of at most 64 x 64 cells take the whole transform in one kernel."""
     from oracle import lagrangian as Lg
     from oracle.objective import Problem as OProblem
     from paper_1703_04446_gb300 import lgnk
