@@ -71,6 +71,11 @@ def _corners(grid: Grid, p: np.ndarray):
     the derivative of that weight along every axis."""
     d = grid.d
     xi = [(p[a] - grid.lo[a]) / grid.h[a] - 0.5 for a in range(d)]
+    # a point on a node in exact arithmetic must take the cell to its right
+    # (floor, Sec. 3.1 derivative of the interpolant); (p - lo) / h - 1/2 can
+    # land a few ulps below the integer, so such values are snapped to it
+    xi = [np.where(np.abs(x - np.rint(x)) <= 16.0 * np.finfo(np.float64).eps * np.maximum(1.0, np.abs(x)),
+                   np.rint(x), x) for x in xi]
     base = [np.floor(x).astype(np.int64) for x in xi]
     frac = [x - b for x, b in zip(xi, base)]
     strides = [int(np.prod(grid.m[:a])) for a in range(d)]

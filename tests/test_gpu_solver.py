@@ -55,6 +55,29 @@ def test_solve_decreases_objective_like_oracle(model, K):
     assert rep["status_name"] in ("ok", "not converged")
 
 
+@pytest.mark.parametrize("matvec", [1, 0])
+def test_first_gauss_newton_step_with_curvature_regularizer(matvec):
+    """With a regularizer other than diffusion the PCG loop ends each product
+    with the separate distribution, stencil and inner-product kernels: one GN
+    step from v = 0 on the curvature case (three time nodes, a domain whose
+    cell widths are not exact in binary), with the assembled J and matrix-free,
+    against the oracle's (PCG 20, tolerance 0.1, Armijo).  At v = 0 every end
+    point is an image node, where both sides take the derivative of the cell
+    to the right."""
+    from paper_1703_04446_gb300 import lgnk
+    from tests._cases import make_case
+    op, gp, a = make_case("2d_transport_ragged_K3")
+    ctx = lgnk.Context(lgnk.Problem(**gp))
+    T, R = (torch.from_numpy(a[k]).cuda() for k in ("T", "R"))
+    _, rep = ctx.solve(T, R, None, max_gn=1, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=0.0, matvec=matvec)
+    _, repo = gauss_newton(op, a["T"].astype(np.float64), a["R"].astype(np.float64), np.zeros(op.vshape),
+                           max_gn=1, gtol=0.0, max_pcg=20, pcg_tol=0.1)
+    assert abs(rep["J0"] - repo["J0"]) <= 1e-5 * repo["J0"]
+    assert abs(rep["g0"] - repo["g0"]) <= 1e-5 * repo["g0"]
+    assert abs(rep["J"] - repo["J"]) <= 1e-4 * repo["J"]
+    assert rep["gn_iters"] == 1 and rep["pcg_iters"] == repo["pcg_iters"]
+
+
 def test_nonfinite_input_is_reported():
     lgnk, prob, op, ins = _setup()
     ctx = lgnk.Context(prob)

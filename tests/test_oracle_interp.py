@@ -57,6 +57,23 @@ def test_interpolate_gradient_central_difference(d):
         np.testing.assert_allclose(grad[a], fd, rtol=1e-5, atol=1e-5)
 
 
+def test_gradient_at_nodes_takes_the_cell_to_the_right():
+    """At a node the interpolant has a kink; the derivative is that of the
+    cell to the right (floor), i.e. the forward difference, with zero beyond
+    the last node.  The domain's h is not exact in binary, so (x - lo)/h - 1/2
+    is not an exact integer at every node before it is snapped."""
+    g = Grid((37, 29), lo=(-0.2, 0.0), hi=(1.1, 1.3))
+    F = np.random.default_rng(5).normal(size=g.shape)      # [y][x]
+    val, grad = interpolate(F, g, cell_centres(g), gradient=True)
+    assert np.allclose(val.reshape(g.shape), F, rtol=0, atol=1e-12)
+    Fp = np.concatenate([F, np.zeros((g.m[1], 1))], axis=1)
+    fx = (Fp[:, 1:] - Fp[:, :-1]) / g.h[0]
+    Fq = np.concatenate([F, np.zeros((1, g.m[0]))], axis=0)
+    fy = (Fq[1:, :] - Fq[:-1, :]) / g.h[1]
+    assert np.allclose(grad[0].reshape(g.shape), fx, rtol=0, atol=1e-9)
+    assert np.allclose(grad[1].reshape(g.shape), fy, rtol=0, atol=1e-9)
+
+
 def test_zero_extension_far_outside():
     g = _grid(2)
     F = np.ones(g.shape)
