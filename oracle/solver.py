@@ -64,7 +64,13 @@ def apply_preconditioner(prob: Problem, r: np.ndarray) -> np.ndarray:
 def pcg(Hfun, b, Minv=None, tol=0.1, maxit=50):
     """Preconditioned conjugate gradients for H x = b from x0 = 0 (Hestenes-Stiefel).
     Stops when |r| <= tol |b| or after maxit iterations, or on non-positive
-    curvature p^T H p <= 0.  Returns (x, iterations, relative residual)."""
+    curvature p^T H p <= 0.  The paper leaves the curvature test to its
+    reference (Nocedal-Wright); read as their line-search Newton-CG: the
+    iterate reached so far is returned, except when the very first direction
+    has non-positive curvature, where the (preconditioned) steepest-descent
+    direction z0 = M^-1 b is returned instead of x = 0, so that the
+    Gauss-Newton step is never empty.  Returns (x, iterations, relative
+    residual); iterations counts the accepted CG steps (0 in that case)."""
     x = np.zeros_like(b)
     r = b.copy()
     nb = np.sqrt(np.sum(b * b))
@@ -78,6 +84,8 @@ def pcg(Hfun, b, Minv=None, tol=0.1, maxit=50):
         Hp = Hfun(p)
         pHp = np.sum(p * Hp)
         if pHp <= 0.0:
+            if it == 1:
+                x = z.copy()        # p = z0 = M^-1 b: preconditioned steepest descent
             it -= 1
             break
         a = rz / pHp
@@ -106,8 +114,10 @@ def armijo(Jfun, v, J0, g, dv, c=1e-4, max_trials=10):
 
 
 def gauss_newton(prob: Problem, T, R, v0, max_gn=10, gtol=1e-3, max_pcg=50,
-                 pcg_tol=0.1, precond=True, log=None):
-    """Inexact Gauss-Newton-Krylov with Armijo (Eq. 11).  Returns (v, report)."""
+                 pcg_tol=0.1, precond=True, log=None, armijo_c=1e-4, max_ls=10):
+    """Inexact Gauss-Newton-Krylov with Armijo (Eq. 11).  Returns (v, report);
+    the report's history holds, per GN iteration, J and |g| at the iterate, the
+    PCG count, the step dv and the step length mu taken."""
     v = np.array(v0, dtype=np.float64, copy=True)
     J, D, S, _ = objective(prob, v, T, R)
     g = gradient(prob, v, T, R)
@@ -119,8 +129,8 @@ def gauss_newton(prob: Problem, T, R, v0, max_gn=10, gtol=1e-3, max_pcg=50,
         if gn <= gtol * g0:
             break
         dv, pit, rel = pcg(lambda p: hessvec(prob, v, T, p), -g, Minv, pcg_tol, max_pcg)
-        mu, Jt = armijo(lambda w: objective(prob, w, T, R)[0], v, J, g, dv)
-        rep["history"].append({"J": J, "g": gn, "pcg": pit, "relres": rel, "mu": mu})
+        mu, Jt = armijo(lambda w: objective(prob, w, T, R)[0], v, J, g, dv, c=armijo_c, max_trials=max_ls)
+        rep["history"].append({"J": J, "g": gn, "pcg": pit, "relres": rel, "mu": mu, "dv": dv})
         rep["pcg_iters"] += pit
         rep["iters"] = it + 1
         if log:
@@ -173,12 +183,14 @@ def prolong_velocity(vc: np.ndarray, cgrid, fgrid) -> np.ndarray:
 
 
 def level_problems(prob: Problem, levels: int):
-    """Problems from coarsest to finest; level l halves both grids (levels - 1 - l) times."""
+    """Problems from coarsest to finest; level l halves both grids (levels - 1 - l) times.
+    Every other field (K, N, model, regularizer and weights, the PIC half-width
+    delta in domain units) is the finest problem's."""
     probs = [prob]
     for _ in range(levels - 1):
         p = probs[0]
         probs.insert(0, Problem(coarse_grid(p.igrid), coarse_grid(p.vgrid), K=p.K, N=p.N, model=p.model,
-                                reg=p.reg, alpha=p.alpha, gamma=p.gamma, mu=p.mu, lam=p.lam))
+                                reg=p.reg, alpha=p.alpha, gamma=p.gamma, mu=p.mu, lam=p.lam, delta=p.delta))
     return probs
 
 

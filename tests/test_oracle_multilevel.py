@@ -61,3 +61,14 @@ def test_multilevel_solve_lowers_objective_on_each_level():
     from oracle.objective import objective
     J_zero = objective(prob, np.zeros(prob.vshape), T, R)[0]
     assert reps[-1]["J0"] < 0.7 * J_zero
+
+
+def test_level_problems_keep_the_particle_width_and_weights():
+    """The coarse levels solve the same continuous problem: the PIC half-width
+    (in domain units), K, N, model, regularizer and weights are the finest
+    level's."""
+    p = Problem(L.Grid((32, 32)), L.Grid((16, 16)), K=3, N=5, model="continuity", reg="elastic", alpha=0.2,
+                gamma=1e-3, mu=0.7, lam=0.4, delta=0.05)
+    for q in level_problems(p, 3):
+        assert (q.K, q.N, q.model, q.reg, q.alpha, q.gamma, q.mu, q.lam, q.delta) == \
+            (3, 5, "continuity", "elastic", 0.2, 1e-3, 0.7, 0.4, 0.05)

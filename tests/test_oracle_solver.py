@@ -5,7 +5,7 @@ import pytest
 
 from oracle import lagrangian as L
 from oracle.objective import Problem, hessvec, objective, reg_operator
-from oracle.solver import apply_preconditioner, gauss_newton, pcg, preconditioner_eigenvalues
+from oracle.solver import apply_preconditioner, armijo, gauss_newton, pcg, preconditioner_eigenvalues
 from paper_1703_04446_gb300 import synth
 
 
@@ -131,3 +131,46 @@ def test_gauss_newton_decreases_objective(model, K):
     assert rep["J"] < 0.5 * rep["J0"]
     assert rep["g"] < rep["g0"]
     assert abs(objective(prob, v, T, R)[0] - rep["J"]) < 1e-14
+
+
+def test_pcg_first_direction_with_nonpositive_curvature_returns_preconditioned_descent():
+    """Line-search Newton-CG (Nocedal-Wright, the paper's reference for the
+    Krylov and line-search settings): when the first direction already has
+    non-positive curvature, the step is the preconditioned steepest-descent
+    direction M^-1 b, not x = 0, and no CG step is counted."""
+    b = np.array([[1.0, -2.0, 0.5], [0.25, 3.0, -1.0]])
+    Minv = lambda r: r / np.array([2.0, 4.0, 8.0])
+    for Hf in (lambda p: -p, lambda p: 0.0 * p):
+        x, it, _ = pcg(Hf, b, Minv, tol=1e-8, maxit=10)
+        assert it == 0
+        np.testing.assert_array_equal(x, Minv(b))
+        x, it, _ = pcg(Hf, b, None, tol=1e-8, maxit=10)
+        assert it == 0
+        np.testing.assert_array_equal(x, b)
+
+
+def test_pcg_later_direction_with_negative_curvature_keeps_the_iterate():
+    """H = diag(1, -1), b = (2, 1): the first direction has curvature 3 > 0,
+    alpha = 5/3; the second direction (20/9, 40/9) has negative curvature, so
+    PCG stops with x1 = (10/3, 5/3) after one step."""
+    H = np.diag([1.0, -1.0])
+    x, it, _ = pcg(lambda p: H @ p, np.array([2.0, 1.0]), None, tol=1e-8, maxit=10)
+    assert it == 1
+    np.testing.assert_allclose(x, [10.0 / 3.0, 5.0 / 3.0], rtol=1e-15)
+
+
+def test_armijo_with_constant_above_one_rejects_every_step_of_a_convex_model():
+    """With c > 1 the sufficient-decrease test asks for more than the linear
+    model promises; on a convex quadratic no step length passes, the search
+    reports mu = 0 and the Gauss-Newton loop stops with the iterate unchanged."""
+    Jf = lambda w: float(np.sum((w - 1.0) ** 2))
+    v = np.zeros(3)
+    g = 2.0 * (v - 1.0)
+    mu, Jt = armijo(Jf, v, Jf(v), g, -g / 2.0, c=2.0, max_trials=10)
+    assert mu == 0.0 and Jt == Jf(v)
+    prob, T, R, _ = _tiny_problem("transport")
+    v0 = np.zeros(prob.vshape)
+    v, rep = gauss_newton(prob, T, R, v0, max_gn=3, gtol=1e-3, max_pcg=20, pcg_tol=0.1, armijo_c=2.0)
+    assert rep["status"] == "line search failed" and rep["iters"] == 1
+    np.testing.assert_array_equal(v, v0)
+    assert rep["J"] == rep["J0"]

@@ -93,3 +93,76 @@ def test_prior_velocity_is_windowed_and_scaled():
     v = synth.prior_velocity(g, 1e-2, 10 / 128, 3)
     assert v.shape == (1, 2, 32, 32)
     assert abs(np.sqrt((v[0] ** 2).sum(0)).max() - 10 / 128) < 1e-6
+
+
+def test_forward_by_hand_on_single_tap_weights():
+    """Architecture pin with c = 1 on 8 x 8 images, written out pixel by pixel
+    without convolutions.  Layer e0 has only its top-left tap (output (i, j)
+    reads input (i - 1, j - 1), zero padding), every other layer only its
+    centre tap, so each layer is a channel mixing at the sampled pixel: stride
+    2 reads pixel (2i, 2j), up2 reads (i // 2, j // 2).  This fixes the layer
+    order, the skip connections, where the ReLUs sit, the strides, the
+    upsampling, the padding and the output scale.  Weights are multiples of
+    1/8 (exact in bfloat16) except one 1/3, which the network rounds to
+    bfloat16: 0.333984375 (8 significant bits, to nearest)."""
+    c, m, scale = 1, 8, 0.05
+    rng = np.random.default_rng(11)
+    shapes = W.layer_shapes(c)
+    Ws, bs = [], []
+    for k, (ci, co, _, _) in enumerate(shapes):
+        Ws.append(rng.integers(-16, 17, size=(co, ci)) / 8.0)
+        bs.append(rng.integers(-8, 9, size=co) / 8.0)
+    Ws[3][5, 2] = 1.0 / 3.0
+    params = []
+    for k, (ci, co, _, _) in enumerate(shapes):
+        w = np.zeros((co, ci, 3, 3))
+        ky, kx = (0, 0) if k == 0 else (1, 1)
+        w[:, :, ky, kx] = Ws[k]
+        params += [w.ravel(), bs[k]]
+    params = np.concatenate(params)
+    T = rng.uniform(-1, 1, size=(m, m))
+    R = rng.uniform(-1, 1, size=(m, m))
+    Wr = [w.copy() for w in Ws]
+    Wr[3][5, 2] = 0.333984375
+    relu = lambda a: max(a, 0.0)
+    e0 = np.zeros((1, m, m))
+    for i in range(m):
+        for j in range(m):
+            t, r = (T[i - 1, j - 1], R[i - 1, j - 1]) if i >= 1 and j >= 1 else (0.0, 0.0)
+            e0[0, i, j] = relu(bs[0][0] + Wr[0][0, 0] * t + Wr[0][0, 1] * r)
+
+    def mix(k, src, co, i, j):
+        return bs[k][co] + sum(Wr[k][co, q] * src[q] for q in range(len(src)))
+
+    def down(k, x, n_out):
+        co_n = Wr[k].shape[0]
+        out = np.zeros((co_n, n_out, n_out))
+        for o in range(co_n):
+            for i in range(n_out):
+                for j in range(n_out):
+                    out[o, i, j] = relu(mix(k, x[:, 2 * i, 2 * j], o, i, j))
+        return out
+
+    e1 = down(1, e0, m // 2)
+    e2 = down(2, e1, m // 4)
+    e3 = down(3, e2, m // 8)
+
+    def up(k, x, skip, n_out):
+        co_n = Wr[k].shape[0]
+        out = np.zeros((co_n, n_out, n_out))
+        for o in range(co_n):
+            for i in range(n_out):
+                for j in range(n_out):
+                    out[o, i, j] = relu(mix(k, x[:, i // 2, j // 2], o, i, j)) + skip[o, i, j]
+        return out
+
+    d2 = up(4, e3, e2, m // 4)
+    d1 = up(5, d2, e1, m // 2)
+    v = np.zeros((2, m // 2, m // 2))
+    for o in range(2):
+        for i in range(m // 2):
+            for j in range(m // 2):
+                v[o, i, j] = scale * mix(6, d1[:, i, j], o, i, j)
+    got = W.forward(params, T[None], R[None], c, scale).numpy()[0]
+    assert np.abs(v).max() > 0.01            # the chosen weights leave a nonzero output
+    np.testing.assert_allclose(got, v, rtol=1e-12, atol=1e-14)
