@@ -120,9 +120,8 @@ lgnk_status lgnk_jtvp(lgnk_ctx* ctx, const float* v, const float* T, const float
  * S = 1/2 dt h_v^d |B v|^2 (dt = 1/(K-1), 1 when stationary).  J, D, S: host
  * doubles (each may be NULL).  grad: NULL or device [n] receiving
  * d_v J = (d_v u1)^T h^d (u1 - R) + alpha dt h_v^d B^T B v (Sec. 3.2).
- * Sums are accumulated in pairs of FP32 values with exact rounding errors
- * (about 48 significant bits) and combined per block in FP64.  Synchronises
- * the stream. */
+ * Sums are accumulated in FP64 per element (each product of FP32 values is
+ * exact in FP64) and combined per block in FP64.  Synchronises the stream. */
 lgnk_status lgnk_objective(lgnk_ctx* ctx, const float* v, const float* T, const float* R,
                            double* J, double* D, double* S, float* grad);
 
@@ -169,10 +168,9 @@ lgnk_status lgnk_precond(lgnk_ctx* ctx, const float* r, float* z);
 lgnk_status lgnk_jacobian_determinant(lgnk_ctx* ctx, const float* v, const float* T, float* det,
                                       double* det_min, double* det_max);
 
-/* Inner product of two device float arrays of length count, summed in pairs
- * of FP32 values with exact rounding errors (about 48 significant bits, a
- * deterministic order) and returned in FP64 on the host.  Synchronises the
- * stream. */
+/* Inner product of two device float arrays of length count, summed in FP64
+ * per element (the products of FP32 values are exact in FP64) in a
+ * deterministic order and returned on the host.  Synchronises the stream. */
 lgnk_status lgnk_dot(lgnk_ctx* ctx, const float* a, const float* b, size_t count, double* out);
 
 /* Profiling.  lgnk_profile(ctx, 1) resets the counters and starts recording a
@@ -211,6 +209,7 @@ typedef struct {
     double seconds;
     int status;           /* lgnk_status of the solve */
     int assembled_gn;     /* GN iterations whose PCG used the assembled J */
+    double last_mu;       /* Armijo step length of the last accepted GN step (0 if none) */
 } lgnk_solve_report;
 
 /* Fill opts with the defaults listed above. */
@@ -219,7 +218,7 @@ void lgnk_solve_opts_default(lgnk_solve_opts* opts);
 /* Inexact Gauss-Newton-Krylov with Armijo line search (Eq. 11): from the
  * initial v_inout[n] (device, overwritten with the result), minimise J for the
  * template T[M] and reference R[M].  Hessian products, preconditioner, vector
- * updates and inner products (FP32 pairs, about 48 bits) run on the device; the host drives the loop
+ * updates and inner products (FP64 sums) run on the device; the host drives the loop
  * and reads one scalar per reduction.  opts may be NULL (defaults); report may
  * be NULL.  Returns LGNK_OK on convergence, LGNK_NOT_CONVERGED at the GN cap,
  * LGNK_LS_FAILED when the line search stalls. */
@@ -263,16 +262,17 @@ lgnk_status lgnk_solve_multilevel(const lgnk_problem* fine, int levels, void* st
  *
  * prob: validated as in lgnk_create; model must be LGNK_TRANSPORT.
  * v[n], T[M] in; u1[M] out (device).  R[M] (device) and D (device, one double)
- * are both NULL or both given: D = h^d/2 |u1 - R|^2, summed in FP32 pairs (about
- * 48 bits) and per block in FP64.
+ * are both NULL or both given: D = h^d/2 |u1 - R|^2, summed in FP64.
  * stream: cudaStream_t (NULL = legacy default stream); the call only enqueues.
  *
  * Scratch: a file-scope device array of 32 MiB (every GPU that loads the
  * library holds it until exit).  A problem whose packed velocity, padded
  * template and partial sums exceed it is rejected with LGNK_ERR_INVALID_ARG
- * (the 128^3 image / 64^3 velocity workload fits).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the one array: calls that
+ * (the 128^3 image / 64^3 velocity workload fits).  Every call made outside a
+ * stream capture looks up the array's device address (cudaGetSymbolAddress),
+ * so a device reset between calls is harmless; a call made while its stream is
+ * being captured reuses the address its device's last uncaptured call found,
+ * so make the first call on a device before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Errors: the status, with detail from
  * lgnk_last_error(NULL).  Allocates nothing. */

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -787,7 +788,9 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
         if ((s = dalloc(ctx, m * P, &ctx->Ci[a])) != LGNK_OK) return fail(s);
     }
     if ((s = dalloc(ctx, ctx->Mv, &ctx->inv_eig)) != LGNK_OK) return fail(s);
-    ctx->npartial = ctx->trace_blocks > 1280 ? ctx->trace_blocks : 1280;  // >= 2 x 608 min/max partials
+    // per-block partials: a trace's blocks, or two per reduction block (two inner
+    // products in one launch; the min and max of det grad y)
+    ctx->npartial = std::max(ctx->trace_blocks, 2 * reduce_block_cap());
     if ((s = dalloc(ctx, (size_t)ctx->npartial, &ctx->partial)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, (size_t)ctx->trace_blocks, &ctx->cpartial)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 8, &ctx->dres)) != LGNK_OK) return fail(s);
@@ -1277,6 +1280,7 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             break;
         }
         CK(cudaMemcpyAsync(v, vt, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        rep.last_mu = mu;
         TRY(obj_grad(v));
         rep.objective_evals++;
         TRY(dot_host(ctx, g, g, n, &gg));

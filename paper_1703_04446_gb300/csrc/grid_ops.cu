@@ -1,6 +1,6 @@
 // Grid utilities of the lgnk library: layout conversion between the ABI layout
-// and the padded packed layout of the tracing kernels, reductions (FP32-pair
-// sums per element, FP64 from the block partials on),
+// and the padded packed layout of the tracing kernels, reductions (the
+// accumulators of fsum.cuh per element, FP64 from the block partials on),
 // regularizer stencils (Sec. 2.1, Sec. 3.2), the per-axis DCT of the spectral
 // preconditioner (Sec. 3.2) and the vector updates of PCG.
 #include <cmath>
@@ -13,7 +13,6 @@
 namespace {
 
 constexpr int kBlock = LGNK_BLOCK;
-constexpr int kReduceBlocks = 608;  // 4 x 152 SMs for grid-stride reductions
 
 inline int nblocks_for(size_t count) {
     return (int)((count + kBlock - 1) / kBlock);
@@ -175,11 +174,11 @@ __device__ __forceinline__ double block_reduce(double x) {
 __global__ void residual_kernel(const float* __restrict__ u1, const float* __restrict__ R, float* __restrict__ rp,
                                 DevGrid g, int d, float scale, double* partial) {
     const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
-    fpair s = fpair_zero();
+    lsum s = lsum_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
         const float ui = u1[i], Ri = R[i];
         const float r = ui - Ri;
-        fpair_add_sqdiff(s, ui, Ri);
+        lsum_add_sqdiff(s, ui, Ri);
         if (rp != nullptr) {
             const int x = (int)(i % g.m[0]);
             const int y = (int)((i / g.m[0]) % g.m[1]);
@@ -188,21 +187,21 @@ __global__ void residual_kernel(const float* __restrict__ u1, const float* __res
             rp[p] = scale * r;
         }
     }
-    s = fpair_block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = fpair_value(s);
+    s = lsum_block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = lsum_value(s);
 }
 
 __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b, size_t count, double* partial) {
-    fpair s = fpair_zero();
+    lsum s = lsum_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        fpair_add_prod(s, a[i], b[i]);
-    s = fpair_block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = fpair_value(s);
+        lsum_add_prod(s, a[i], b[i]);
+    s = lsum_block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = lsum_value(s);
 }
 
 // One or two inner products sharing the first operand, finished in the same
-// launch: every block writes its partial sums (FP32 pairs, stored in the FP64
-// partial buffer's slots), and the last block to finish (a counter, reset by
+// launch: every block writes its partial sums (FP64, in the partial buffer's
+// slots), and the last block to finish (a counter, reset by
 // that block) adds the partials in a fixed order (deterministic) into
 // sc[slot_b] (a.b) and sc[slot_c] (a.c, when c is given), then the PCG step
 // lengths of step `mode` (-1: none), in FP64, from the inner products in sc
@@ -221,47 +220,43 @@ __device__ __forceinline__ void pcg_step_lengths(double* sc, float* f, int mode)
     }
 }
 
-// Second half of the fused inner products: block sums of the per-thread pairs
-// s (a.b) and, when `two`, t (a.c); every block writes its partials and the
-// last block to finish adds them in a fixed order into sc[slot_b] (sc[slot_c])
-// and applies pcg_step_lengths(mode).  Every thread of every block calls it.
-__device__ __forceinline__ void dot_blocks_finish(fpair s, fpair t, bool two, double* partial, unsigned* counter,
+// Second half of the fused inner products: block sums of the per-thread
+// accumulators s (a.b) and, when `two`, t (a.c); every block writes its
+// partials (FP64) and the last block to finish adds them in a fixed order
+// (FP64, deterministic) into sc[slot_b] (sc[slot_c]) and applies
+// pcg_step_lengths(mode).  Every thread of every block calls it.
+__device__ __forceinline__ void dot_blocks_finish(lsum s, lsum t, bool two, double* partial, unsigned* counter,
                                                   double* sc, int slot_b, int slot_c, int mode, float* f) {
-    s = fpair_block_sum(s);
+    s = lsum_block_sum(s);
     if (two) {
-        __syncthreads();      // fpair_block_sum's shared slots are reused
-        t = fpair_block_sum(t);
+        __syncthreads();      // lsum_block_sum's shared slots are reused
+        t = lsum_block_sum(t);
     }
-    float* pp = reinterpret_cast<float*>(partial);    // pair j at floats 2j, 2j + 1
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        pp[2 * blockIdx.x] = s.hi;
-        pp[2 * blockIdx.x + 1] = s.lo;
-        if (two) {
-            pp[2 * (gridDim.x + blockIdx.x)] = t.hi;
-            pp[2 * (gridDim.x + blockIdx.x) + 1] = t.lo;
-        }
+        partial[blockIdx.x] = lsum_value(s);
+        if (two) partial[gridDim.x + blockIdx.x] = lsum_value(t);
         __threadfence();
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const volatile float* vp = pp;
-    fpair u = fpair_zero(), w = fpair_zero();
+    const volatile double* vp = partial;
+    double u = 0.0, w = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        fpair_add(u, fpair{vp[2 * i], vp[2 * i + 1]});
-        if (two) fpair_add(w, fpair{vp[2 * (gridDim.x + i)], vp[2 * (gridDim.x + i) + 1]});
+        u += vp[i];
+        if (two) w += vp[gridDim.x + i];
     }
     __syncthreads();          // the first block sums' shared slots are reused
-    u = fpair_block_sum(u);
+    u = block_reduce(u);
     if (two) {
         __syncthreads();
-        w = fpair_block_sum(w);
+        w = block_reduce(w);
     }
     if (threadIdx.x == 0) {
-        sc[slot_b] = fpair_value(u);
-        if (two) sc[slot_c] = fpair_value(w);
+        sc[slot_b] = u;
+        if (two) sc[slot_c] = w;
         pcg_step_lengths(sc, f, mode);
         *counter = 0u;
     }
@@ -270,11 +265,11 @@ __device__ __forceinline__ void dot_blocks_finish(fpair s, fpair t, bool two, do
 __global__ void dot_fused_kernel(const float* __restrict__ a, const float* __restrict__ b,
                                  const float* __restrict__ c, size_t count, double* partial, unsigned* counter,
                                  double* sc, int slot_b, int slot_c, int mode, float* f) {
-    fpair s = fpair_zero(), t = fpair_zero();
+    lsum s = lsum_zero(), t = lsum_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
         const float ai = a[i];
-        fpair_add_prod(s, ai, b[i]);
-        if (c != nullptr) fpair_add_prod(t, ai, c[i]);
+        lsum_add_prod(s, ai, b[i]);
+        if (c != nullptr) lsum_add_prod(t, ai, c[i]);
     }
     dot_blocks_finish(s, t, c != nullptr, partial, counter, sc, slot_b, slot_c, mode, f);
 }
@@ -294,7 +289,7 @@ __global__ void hess_finish_kernel(const float* __restrict__ Gp, const float* __
     const size_t nodes = padded_size(g);
     const size_t total = Mv * K;
     const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
-    fpair dsum = fpair_zero();
+    lsum dsum = lsum_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t sn = i % Mv;
         const int j = (int)(i / Mv);
@@ -333,10 +328,10 @@ __global__ void hess_finish_kernel(const float* __restrict__ Gp, const float* __
             if (gamma != 0.0f) r = fmaf(gamma, xi, r);
             r += gscale * acc[q];
             Hp[k] = r;
-            fpair_add_prod(dsum, xi, r);
+            lsum_add_prod(dsum, xi, r);
         }
     }
-    dot_blocks_finish(dsum, fpair_zero(), false, partial, counter, sc, 2, 2, 0, f);
+    dot_blocks_finish(dsum, lsum_zero(), false, partial, counter, sc, 2, 2, 0, f);
 }
 
 // x += f[0] p and r += f[1] Hp (the PCG updates with alpha, -alpha)
@@ -1136,11 +1131,32 @@ cudaError_t launch_repad_image(float* acc, const DevGrid& g, int d, float scale,
     return cudaGetLastError();
 }
 
+// Blocks of the grid-stride reductions: four per SM of the current device
+// (the SM count is read once per device ordinal).
+int reduce_block_cap() {
+    static int cap[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 4 * 152;
+    }
+    if (cap[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        cap[dev] = 4 * sms;
+    }
+    return cap[dev];
+}
+
 int residual_blocks(const DevGrid& g, int d) {
     (void)d;
     const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
     const int b = nblocks_for(M);
-    return b < kReduceBlocks ? b : kReduceBlocks;
+    const int cap = reduce_block_cap();
+    return b < cap ? b : cap;
 }
 
 cudaError_t launch_residual(const float* u1, const float* R, float* rp, const DevGrid& g, int d, float scale,
@@ -1156,7 +1172,8 @@ cudaError_t launch_reduce(const double* partial, int count, double* out, cudaStr
 
 int dot_blocks(size_t count) {
     const int b = nblocks_for(count);
-    return b < kReduceBlocks ? (b > 0 ? b : 1) : kReduceBlocks;
+    const int cap = reduce_block_cap();
+    return b < cap ? (b > 0 ? b : 1) : cap;
 }
 
 cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, size_t count, double* partial,

@@ -65,7 +65,7 @@ struct TraceArgs {
     float* yout;              // optional end points [d][M]
     float* acc;               // continuity splat accumulator (padded image)
     void* G;                  // gradient accumulator slices [m][zp][yp][xp] of float4 (3D) / float2 (2D)
-    double* partial;          // per-block partial sums of res^2 (FP32-pair sums, stored in FP64)
+    double* partial;          // per-block partial sums of res^2 (FP64)
     // MODE_ASM (transport): rows of the assembled J, entry-major [e][voxel]
     long long* ekey;          // element of the lower corner of the entry's cell in the slice gradient space
     float* eblk;              // [e][corner][component][voxel]: sum of w_corner * mu over the cell's stages
@@ -116,6 +116,8 @@ cudaError_t launch_repad_image(float* acc, const DevGrid& g, int d, float scale,
 cudaError_t launch_residual(const float* u1, const float* R, float* rp, const DevGrid& g, int d,
                             float scale, double* partial, int nblocks, cudaStream_t s);
 int residual_blocks(const DevGrid& g, int d);
+// blocks of the grid-stride reductions (4 per SM of the current device)
+int reduce_block_cap();
 cudaError_t launch_reduce(const double* partial, int count, double* out, cudaStream_t s);
 cudaError_t launch_dot(const float* a, const float* b, size_t count, double* partial, int nblocks,
                        cudaStream_t s);

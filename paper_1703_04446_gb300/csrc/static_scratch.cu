@@ -26,8 +26,14 @@ std::mutex g_scratch_mutex;
 
 // Device address of g_static_scratch on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
-lgnk_status scratch_address(void** out) {
+// cudaGetSymbolAddress, with that device current.  A reset of the device
+// (cudaDeviceReset, or its primary context destroyed and created again)
+// reloads the module and can move the array, so every call made outside a
+// stream capture looks the address up again; a call made while `s` is being
+// captured uses the address its device's last uncaptured call found (the
+// lookup may load the module, which a capture does not allow), so the first
+// call on a device must come before any capture.
+lgnk_status scratch_address(cudaStream_t s, void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -38,8 +44,14 @@ lgnk_status scratch_address(void** out) {
         lgnk_internal_set_error("device index beyond the static scratch table");
         return LGNK_ERR_INVALID_ARG;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) {
+        lgnk_internal_set_error(cudaGetErrorString(e));
+        return LGNK_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (g_scratch_dev[dev] == nullptr) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) {
@@ -47,6 +59,9 @@ lgnk_status scratch_address(void** out) {
             return LGNK_ERR_CUDA;
         }
         g_scratch_dev[dev] = p;
+    } else if (g_scratch_dev[dev] == nullptr) {
+        lgnk_internal_set_error("the first allocation-free call on a device must come before any stream capture");
+        return LGNK_ERR_INVALID_ARG;
     }
     *out = g_scratch_dev[dev];
     return LGNK_OK;
@@ -98,14 +113,14 @@ extern "C" lgnk_status lgnk_forward_transport_static(const lgnk_problem* prob, c
         lgnk_internal_set_error(msg);
         return LGNK_ERR_INVALID_ARG;
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* base = nullptr;
-    lgnk_status st = scratch_address(reinterpret_cast<void**>(&base));
+    lgnk_status st = scratch_address(s, reinterpret_cast<void**>(&base));
     if (st != LGNK_OK) return st;
     void* Vp = base;
     float* Tp = reinterpret_cast<float*>(base + vbytes);
     double* partial = reinterpret_cast<double*>(base + vbytes + tbytes);
     double* sum = reinterpret_cast<double*>(base + vbytes + tbytes + pbytes);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // Every scratch byte a launch reads is written earlier in the same call
     // (packing writes pads and interiors, each block writes its partial), so

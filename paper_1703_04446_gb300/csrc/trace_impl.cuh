@@ -1145,7 +1145,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
     int idx[3];
     voxel_index<D>(A, idx);
     const bool active = idx[0] < A.ig.m[0] && idx[1] < A.ig.m[1] && (D == 2 || idx[2] < A.ig.m[2]);
-    fpair ssd = fpair_zero();  // res^2 of this thread's voxel (FWD with R, OBJGRAD, ASM with R)
+    lsum ssd = lsum_zero();  // res^2 of this thread's voxel (FWD with R, OBJGRAD, ASM with R)
     int entries = 0;           // MODE_ASM: blocks of this thread's row
 
     SC S;
@@ -1195,7 +1195,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
             if (MODE == MODE_FWD) {
                 const float val = sample_image<D, false>(A.ig, si, A.Tp, u, nullptr);
                 A.u1[vox] = val;
-                if (A.R != nullptr) fpair_add_sqdiff(ssd, val, A.R[vox]);
+                if (A.R != nullptr) lsum_add_sqdiff(ssd, val, A.R[vox]);
             } else if (MODE == MODE_JVP) {
                 sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 float du = 0.0f;
@@ -1221,14 +1221,14 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
                 for (int a = 0; a < D; ++a) lam[a] = gT[a];
                 if (A.R != nullptr) {     // with the objective: SSD and the gradient's weights h^d res
                     const float Rv = A.R[vox];
-                    fpair_add_sqdiff(ssd, val, Rv);
+                    lsum_add_sqdiff(ssd, val, Rv);
                     A.u1[vox] = A.cellvol * (val - Rv);
                 }
             } else {  // MODE_OBJGRAD
                 const float val = sample_image<D, true>(A.ig, si, A.Tp, u, gT);
                 if (A.u1 != nullptr) A.u1[vox] = val;
                 const float Rv = A.R[vox];
-                fpair_add_sqdiff(ssd, val, Rv);
+                lsum_add_sqdiff(ssd, val, Rv);
                 const float s = A.cellvol * (val - Rv);
 #pragma unroll
                 for (int a = 0; a < D; ++a) lam[a] = s * gT[a];
@@ -1272,14 +1272,16 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
 
     if (MODE == MODE_OBJGRAD || MODE == MODE_FWD || MODE == MODE_ASM) {
         if (A.partial != nullptr) {
-            const fpair s = fpair_block_sum(ssd);
-            if (threadIdx.x == 0) A.partial[blockIdx.x] = fpair_value(s);
+            const lsum s = lsum_block_sum(ssd);
+            if (threadIdx.x == 0) A.partial[blockIdx.x] = lsum_value(s);
         }
     }
     if (MODE == MODE_ASM && A.cpartial != nullptr) {
-        __syncthreads();      // fpair_block_sum's shared slots are reused
-        const fpair c = fpair_block_sum(fpair{(float)entries, 0.0f});   // exact: at most 256 x 16 blocks
-        if (threadIdx.x == 0) A.cpartial[blockIdx.x] = fpair_value(c);
+        __syncthreads();      // lsum_block_sum's shared slots are reused
+        lsum c = lsum_zero();
+        lsum_add(c, (float)entries);
+        c = lsum_block_sum(c);   // exact: at most 256 x 16 blocks
+        if (threadIdx.x == 0) A.cpartial[blockIdx.x] = lsum_value(c);
     }
 }
 

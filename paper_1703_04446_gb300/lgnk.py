@@ -60,7 +60,7 @@ class _SolveReport(ctypes.Structure):
                 ("objective_evals", ctypes.c_int), ("J0", ctypes.c_double), ("J", ctypes.c_double),
                 ("D", ctypes.c_double), ("S", ctypes.c_double), ("g0", ctypes.c_double),
                 ("g", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
-                ("assembled_gn", ctypes.c_int)]
+                ("assembled_gn", ctypes.c_int), ("last_mu", ctypes.c_double)]
 
 
 EXPORTS = {
@@ -437,7 +437,7 @@ def lgnk_jacobian_determinant(ctx: Context, v, T, field=True):
 
 
 def lgnk_dot(ctx: Context, a, b):
-    """Inner product of two float32 device tensors (FP32-pair sums, about 48 bits), as a Python float."""
+    """Inner product of two float32 device tensors, summed in FP64 on the device, as a Python float."""
     if a.numel() != b.numel():
         raise ValueError("size mismatch")
     for t in (a, b):

@@ -80,3 +80,75 @@ def test_objective_gradient_consistency_full_size(full):
     fd = (Jp - Jm) / (2 * e)
     an = float((g.double() * t["dv"].double()).sum())
     assert abs(an - fd) <= 2e-3 * abs(an)
+
+
+def test_jtvp_on_sampled_support(full):
+    """J^T r element by element at full size: r is zero except on the 3000
+    sampled voxels, so J^T r is the sum of exactly those characteristics'
+    adjoint sweeps, which the oracle computes one by one."""
+    ctx, t, ins, dv, ig, vg, sample, wl = full
+    rng = np.random.default_rng(21)
+    r = np.zeros(ig.size, dtype=np.float32)
+    r[sample] = rng.normal(size=sample.size).astype(np.float32)
+    gv = ctx.jtvp(t["v"], t["T"], torch.from_numpy(r.reshape(ig.shape)).cuda()).cpu().numpy().astype(np.float64)
+    v64, T64 = ins["v0"].astype(np.float64), ins["T"].astype(np.float64)
+    x = L.cell_centres(ig)[:, sample]
+    y, _, hist = L.characteristics(v64, vg, x, wl.rk4_steps, -1, keep=True)
+    _, gT = L.interpolate(T64, ig, y, gradient=True)
+    ref = L.characteristics_adjoint(v64, vg, hist, wl.rk4_steps, -1, gT * r[sample].astype(np.float64))
+    assert np.linalg.norm(gv - ref) <= TOL * np.linalg.norm(ref)
+
+
+def _sparse_template(ins, ig, wl, n_spots=12, radius=2, seed=31):
+    """The benchmark's template kept only in small balls around a few interior
+    points (zero elsewhere), and the voxels whose characteristic can end where
+    its interpolated gradient is nonzero: within the balls' radius, plus the
+    largest displacement the velocity can make in unit time, plus one cell."""
+    rng = np.random.default_rng(seed)
+    m = np.array(ig.m)
+    centres = rng.integers(16, m - 16, size=(n_spots, 3))
+    z, y, x = np.meshgrid(*(np.arange(k) for k in reversed(ig.m)), indexing="ij")
+    idx = np.stack([x, y, z])
+    d2 = np.min([np.sum((idx - c.reshape(3, 1, 1, 1)) ** 2, axis=0) for c in centres], axis=0)
+    T = np.where(d2 <= radius ** 2, ins["T"], 0.0).astype(np.float32)
+    vmax = float(np.sqrt(np.sum(ins["v0"].astype(np.float64) ** 2, axis=1)).max())
+    reach = radius + vmax / min(ig.h) + 2.0
+    support = np.flatnonzero(d2.ravel() <= reach ** 2)
+    return T, support
+
+
+@pytest.mark.parametrize("assembled", [False, True])
+def test_hessvec_on_sparse_template(full, assembled):
+    """The fused matrix-free Gauss-Newton matvec (and the assembled one) at full
+    size, element by element: with a template that is zero outside a few small
+    balls, row i of J vanishes unless characteristic i ends next to a ball, so
+    H dv = sum over those voxels of J_i^T h^d J_i dv + alpha A dv + gamma dv,
+    which the oracle computes voxel by voxel."""
+    ctx, t, ins, dv, ig, vg, sample, wl = full
+    Ts, support = _sparse_template(ins, ig, wl)
+    tTs = torch.from_numpy(Ts).cuda()
+    if assembled:
+        ctx.assemble(t["v"], tTs)
+        Hp = ctx.hessvec_assembled(t["dv"])
+    else:
+        Hp = ctx.hessvec(t["v"], tTs, t["dv"])
+    Hp = Hp.cpu().numpy().astype(np.float64)
+    # rows outside the support are exactly zero on the GPU as well
+    du = ctx.jvp(t["v"], tTs, t["dv"]).cpu().numpy().ravel()
+    outside = np.ones(ig.size, dtype=bool)
+    outside[support] = False
+    assert not np.any(du[outside])
+    v64, T64, dv64 = ins["v0"].astype(np.float64), Ts.astype(np.float64), dv.astype(np.float64)
+    x = L.cell_centres(ig)[:, support]
+    y, dy, hist = L.characteristics(v64, vg, x, wl.rk4_steps, -1, dv=dv64, keep=True)
+    _, gT = L.interpolate(T64, ig, y, gradient=True)
+    du_ref = np.sum(gT * dy, axis=0)
+    g = L.characteristics_adjoint(v64, vg, hist, wl.rk4_steps, -1, ig.cell_volume * du_ref * gT)
+    op = OP(ig, vg, K=1, N=wl.rk4_steps, alpha=wl.alpha, gamma=1e-3)
+    ref = g + wl.alpha * reg_operator(op, dv64) + 1e-3 * dv64
+    data = g
+    assert np.linalg.norm(data) > 1e-3 * np.linalg.norm(ref)      # the data term is not negligible
+    assert np.linalg.norm(Hp - ref) <= TOL * np.linalg.norm(ref)
+    # the data term alone, against its own norm
+    reg_only = wl.alpha * reg_operator(op, dv64) + 1e-3 * dv64
+    assert np.linalg.norm((Hp - reg_only) - data) <= 1e-4 * np.linalg.norm(data)

@@ -62,3 +62,38 @@ def test_hessian_symmetry_full_size(case):
     a = float((t["p2"].double() * Hp.double()).sum())
     b = float((t["dv"].double() * Hq.double()).sum())
     assert abs(a - b) <= TOL * (abs(a) + abs(b))
+
+
+def _sampled_particles(wl, ins, n=1500, seed=12):
+    """A template whose mass sits only on n sampled particles (zero elsewhere):
+    the push-forward, its derivative and its transpose then involve exactly
+    those characteristics, which the oracle traces one by one."""
+    ig = L.Grid(wl.image.m, wl.image.lo, wl.image.hi)
+    sample = np.random.default_rng(seed).choice(ig.size, size=n, replace=False)
+    Ts = np.zeros(ig.size, dtype=np.float32)
+    Ts[sample] = ins["T"].ravel()[sample] + np.float32(0.5 * ins["T"].max())
+    return ig, sample, Ts
+
+
+def test_products_on_sampled_particles(case):
+    """u1, J dv and J^T r element by element at full size (the whole image and
+    the whole velocity gradient), with the template's mass on sampled particles."""
+    name, wl, ins, ctx, t = case
+    ig, sample, Ts = _sampled_particles(wl, ins)
+    vg = L.Grid(wl.velocity.m, wl.velocity.lo, wl.velocity.hi)
+    tTs = torch.from_numpy(Ts.reshape(ig.shape)).cuda()
+    u1 = ctx.forward(t["v"], tTs).cpu().numpy().astype(np.float64).ravel()
+    du = ctx.jvp(t["v"], tTs, t["dv"]).cpu().numpy().astype(np.float64).ravel()
+    gv = ctx.jtvp(t["v"], tTs, t["r"]).cpu().numpy().astype(np.float64)
+    v64, dv64 = ins["v0"].astype(np.float64), t["dv"].cpu().numpy().astype(np.float64)
+    x = L.cell_centres(ig)[:, sample]
+    mass = Ts[sample].astype(np.float64)
+    y, dy, _ = L.characteristics(v64, vg, x, wl.rk4_steps, +1, dv=dv64)
+    u1_ref = L.scatter(mass, ig, y).ravel()
+    du_ref = L.scatter_gradient(mass, dy, ig, y).ravel()
+    assert np.linalg.norm(u1 - u1_ref) <= TOL * np.linalg.norm(u1_ref)
+    assert np.linalg.norm(du - du_ref) <= TOL * np.linalg.norm(du_ref)
+    _, _, hist = L.characteristics(v64, vg, x, wl.rk4_steps, +1, keep=True)
+    _, gr = L.interpolate(t["r"].cpu().numpy().astype(np.float64), ig, y, gradient=True)
+    gv_ref = L.characteristics_adjoint(v64, vg, hist, wl.rk4_steps, +1, gr * mass)
+    assert np.linalg.norm(gv - gv_ref) <= TOL * np.linalg.norm(gv_ref)

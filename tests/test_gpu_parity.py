@@ -126,10 +126,10 @@ def test_adjoint_identity_on_gpu(name):
 
 
 def test_dot_accumulates_beyond_fp32():
-    """Inner products are summed in FP32 pairs (hi + lo with exact rounding
-    errors): a sum that FP32 alone would round is exact, and a random ragged
-    case lands within 1e-12 of sum |a_i b_i| from the exactly rounded sum of the
-    exact FP64 products (FP32 accumulation misses by about 3e-8 here)."""
+    """Inner products are summed in FP64 per element: a sum that FP32 alone
+    would round is exact, and a random ragged case lands within 1e-12 of
+    sum |a_i b_i| from the exactly rounded sum of the exact FP64 products
+    (FP32 accumulation misses by about 3e-8 here)."""
     import math
     ctx, t = _gpu("2d_transport_64")
     a = torch.full((1 << 20,), 1.0 + 2.0 ** -20, device="cuda")
@@ -144,6 +144,33 @@ def test_dot_accumulates_beyond_fp32():
     ref = math.fsum(prods)
     got = ctx.dot(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     assert abs(got - ref) <= 1e-12 * float(np.abs(prods).sum())
+
+
+@pytest.mark.parametrize("lo,hi", [(-20.0, -12.0), (-23.0, -19.0), (15.0, 20.0)])
+def test_dot_keeps_fp64_range(lo, hi):
+    """Entries of 1e-20 to 1e-12 (the size of residuals and directions late in
+    a PCG solve on fine grids) have products of 1e-40 to 1e-24, below FP32's
+    normal range; entries near 1e20 have products beyond FP32's largest value.
+    Both sum to within 1e-12 of sum |a_i b_i| of math.fsum over the exact
+    products, and the SSD of such images keeps its value too."""
+    import math
+    ctx, t = _gpu("2d_transport_64")
+    rng = np.random.default_rng(12)
+    n = (1 << 18) + 77
+    x = (rng.normal(size=n) * 10.0 ** rng.uniform(lo, hi, size=n)).astype(np.float32)
+    y = (rng.normal(size=n) * 10.0 ** rng.uniform(lo, hi, size=n)).astype(np.float32)
+    prods = x.astype(np.float64) * y.astype(np.float64)
+    ref = math.fsum(prods)
+    got = ctx.dot(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    assert abs(got - ref) <= 1e-12 * float(np.abs(prods).sum())
+    assert ctx.dot(torch.from_numpy(x).cuda(), torch.from_numpy(x).cuda()) == \
+        pytest.approx(math.fsum(x.astype(np.float64) ** 2), rel=1e-12)
+    # SSD at v = 0, where u1 = T exactly (every characteristic ends on its node)
+    T, R = x[:4096].reshape(64, 64), y[:4096].reshape(64, 64)
+    _, D, _ = ctx.objective(torch.zeros((1, 2, 32, 32), device="cuda"), torch.from_numpy(T.copy()).cuda(),
+                            torch.from_numpy(R.copy()).cuda())
+    d = T.astype(np.float64) - R.astype(np.float64)
+    assert D == pytest.approx(0.5 / 64 ** 2 * math.fsum((d * d).ravel()), rel=1e-12)
 
 
 def test_zero_velocity_is_identity():

@@ -1,0 +1,118 @@
+"""Gauss-Newton iterates of lgnk_solve against the oracle, iterate by iterate.
+
+The GN problem is non-convex and the FP32 GPU path and the FP64 oracle may
+drift apart over many steps, so each GPU iterate is handed to the oracle and
+both take the next step from that same point: the objective and gradient
+norm at the iterate, the step, and the objective after the step are compared
+(the GPU solve runs one GN iteration per call from the iterate it is given).
+Tolerances: objectives 1e-5 at a given iterate and 1e-4 after a step (the
+stated bar), gradient norms 1e-5, steps 1e-3 (twenty FP32 CG iterations
+against FP64 ones)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lagrangian as L
+from oracle.objective import Problem as OP, gradient, hessvec, objective
+from oracle.solver import apply_preconditioner, gauss_newton
+from paper_1703_04446_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(name, seed=0):
+    from paper_1703_04446_gb300 import lgnk
+    ins = synth.make_inputs(name, seed=seed)
+    wl = ins["workload"]
+    prob = lgnk.Problem.from_workload(wl)
+    op = OP(L.Grid(wl.image.m, wl.image.lo, wl.image.hi), L.Grid(wl.velocity.m, wl.velocity.lo, wl.velocity.hi),
+            K=wl.time_nodes, N=wl.rk4_steps, model=wl.model, reg=wl.regularizer, alpha=wl.alpha, gamma=wl.gamma,
+            mu=wl.extra.get("mu", 1.0), lam=wl.extra.get("lam", 0.0))
+    ctx = lgnk.Context(prob)
+    T64, R64 = ins["T"].astype(np.float64), ins["R"].astype(np.float64)
+    tT, tR = (torch.from_numpy(ins[k]).cuda() for k in ("T", "R"))
+    return ctx, op, T64, R64, tT, tR
+
+
+@pytest.mark.parametrize("matvec", [1, 0])
+def test_transport_64_iterates_follow_the_oracle(matvec):
+    """2D intensity-preserving workload (64^2, 10 GN / 20 PCG): every GN step
+    from the GPU's own iterate, with the assembled J and matrix-free."""
+    ctx, op, T64, R64, tT, tR = _setup("2d_transport_64")
+    v = torch.zeros(op.vshape, device="cuda")
+    g_first = None
+    for k in range(10):
+        v_next, rep = ctx.solve(tT, tR, v, max_gn=1, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=0.0, matvec=matvec)
+        v64 = v.cpu().numpy().astype(np.float64)
+        vo, repo = gauss_newton(op, T64, R64, v64, max_gn=1, gtol=0.0, max_pcg=20, pcg_tol=0.1)
+        h = repo["history"][0]
+        assert abs(rep["J0"] - h["J"]) <= 1e-5 * h["J"], k
+        assert abs(rep["g0"] - h["g"]) <= 1e-5 * h["g"], k
+        g_first = g_first or h["g"]
+        step = (v_next.cpu().numpy().astype(np.float64) - v64)
+        ref = h["mu"] * h["dv"]
+        assert rep["last_mu"] == h["mu"], k
+        assert np.linalg.norm(step - ref) <= 1e-3 * np.linalg.norm(ref), k
+        assert abs(rep["pcg_iters"] - h["pcg"]) <= 1, k
+        assert abs(rep["J"] - repo["J"]) <= 1e-4 * repo["J"], k
+        v = v_next
+        if h["g"] <= 1e-3 * g_first:
+            break
+
+
+def test_transport_64_final_objective_of_independent_solves():
+    """Both solvers from v = 0 on their own (10 GN / 20 PCG, stop at a 1e-3
+    gradient-norm drop): the final objectives agree to 1e-4."""
+    ctx, op, T64, R64, tT, tR = _setup("2d_transport_64")
+    _, rep = ctx.solve(tT, tR, None, max_gn=10, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=1e-3)
+    _, repo = gauss_newton(op, T64, R64, np.zeros(op.vshape), max_gn=10, gtol=1e-3, max_pcg=20, pcg_tol=0.1)
+    assert abs(rep["J0"] - repo["J0"]) <= 1e-5 * repo["J0"]
+    assert abs(rep["J"] - repo["J"]) <= 1e-4 * repo["J"]
+
+
+def test_continuity_256_iterates_under_the_oracle():
+    """2D mass-preserving workload (256^2, 5 time nodes, N = 16, elastic):
+    three GN steps from the GPU's iterates.  At each iterate the oracle's J and
+    |g| match; the GPU's step is an inexact Newton step of the oracle's own
+    system (|H x + g| <= 0.1 |g| unless PCG hit its cap, and x a descent
+    direction); the objective after the step matches the oracle's objective at
+    the GPU's new iterate.  (The oracle's PCG itself takes minutes here.)"""
+    ctx, op, T64, R64, tT, tR = _setup("2d_continuity_256")
+    v = torch.zeros(op.vshape, device="cuda")
+    for k in range(3):
+        v_next, rep = ctx.solve(tT, tR, v, max_gn=1, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=0.0)
+        v64 = v.cpu().numpy().astype(np.float64)
+        J = objective(op, v64, T64, R64)[0]
+        g = gradient(op, v64, T64, R64)
+        gn = float(np.linalg.norm(g))
+        assert abs(rep["J0"] - J) <= 1e-5 * J, k
+        assert abs(rep["g0"] - gn) <= 1e-5 * gn, k
+        assert rep["last_mu"] > 0.0, k
+        vn64 = v_next.cpu().numpy().astype(np.float64)
+        x = (vn64 - v64) / rep["last_mu"]
+        res = np.linalg.norm(hessvec(op, v64, T64, x) + g)
+        if rep["pcg_iters"] < 20:
+            assert res <= 0.1 * gn * 1.05, k
+        assert res < gn and float(np.sum(g * x)) < 0.0, k
+        Jn = objective(op, vn64, T64, R64)[0]
+        assert abs(rep["J"] - Jn) <= 1e-5 * Jn, k
+        assert rep["J"] < rep["J0"], k
+        v = v_next
+
+
+def test_line_search_forced_to_fail_keeps_the_iterate():
+    """A sufficient-decrease constant above one (c = 2) asks for more than the
+    quadratic model gives, so every trial fails: the solve reports
+    LGNK_LS_FAILED after one GN iteration and returns the iterate it was given,
+    bit for bit, as the oracle's Gauss-Newton does."""
+    ctx, op, T64, R64, tT, tR = _setup("2d_transport_64")
+    v0 = torch.from_numpy(synth.random_velocity(synth.WORKLOADS["2d_transport_64"].velocity, 1, 0.01, 4)
+                          .astype(np.float32)).cuda()
+    v, rep = ctx.solve(tT, tR, v0, max_gn=3, max_pcg=20, pcg_rtol=0.1, gn_grad_rtol=1e-3, armijo_c=2.0)
+    assert rep["status"] == 6 and rep["status_name"] == "line search failed"
+    assert rep["gn_iters"] == 1 and rep["last_mu"] == 0.0
+    assert torch.equal(v, v0)
+    assert rep["J"] == rep["J0"]
+    _, repo = gauss_newton(op, T64, R64, v0.cpu().numpy().astype(np.float64), max_gn=3, gtol=1e-3, max_pcg=20,
+                           pcg_tol=0.1, armijo_c=2.0)
+    assert repo["status"] == "line search failed" and repo["iters"] == 1
