@@ -406,29 +406,33 @@ __device__ __forceinline__ void scatter_add(const DevGrid& g, BlockScatter<D>& S
     }
 }
 
-// Destination of the adjoint contributions when a row of J is assembled: a
-// per-thread table of (slice, cell) blocks, each the 2^d corner vectors
-// sum_stages w_c(f) mu.  A trajectory stays within a few velocity cells, so a
-// row has few blocks; a row that needs more than CAP sets `overflow`.
+// Destination of the adjoint contributions when a row of J is assembled: the
+// row's (slice, cell) blocks, each the 2^d corner vectors sum_stages
+// w_c(f) mu.  A trajectory stays within a few velocity cells, so a row has
+// few blocks; a row that needs more than CAP sets `overflow`.  The keys live
+// in a per-thread table (local memory); the blocks go straight to the row's
+// slots of the global ELL array, entry j of voxel i at [j][i][corner][q], and
+// a block met again is read back, added to and stored by the same thread.
 template <int D>
 struct AsmTable {
     static constexpr int CAP = D == 3 ? 16 : 32;
     long long key[CAP];
-    float blk[CAP][(1 << D) * D];
     int n;
     bool overflow;
 };
 
-// The table is indexed by entry and lives in local memory; the block of the
-// current cell is a separate object, indexed statically, so that it stays in
-// registers until the cell changes (kept in the table's struct it was placed
-// in local memory with it: 1.23 ms for the 128^3 assembly, 0.79 ms apart).
+// The block of the current cell is kept in registers (pblk) until the cell
+// changes; it is then committed to the row (kept in the table's local array
+// it was placed in local memory: 1.23 ms for the 128^3 assembly, 0.79 ms apart).
 template <int D>
 struct AsmRow {
     static constexpr int CAP = AsmTable<D>::CAP;
+    static constexpr int B = (1 << D) * D;
     AsmTable<D>* tab;
+    float* blk;               // entry 0 of this voxel's blocks in the ELL array
+    size_t stride;            // floats from entry j to entry j + 1 of one voxel
     long long pkey;
-    float pblk[(1 << D) * D];
+    float pblk[B];
 };
 
 template <int D>
@@ -436,28 +440,38 @@ __device__ __forceinline__ void scatter_init(AsmRow<D>& S, void*) {
     S.pkey = -1;
 }
 
-// Add the pending block to the table entry of its cell (a new entry if the
+// Add the pending block to the row's entry of its cell (a new entry if the
 // row has none yet).
 template <int D>
 __device__ __forceinline__ void asm_commit(AsmRow<D>& S) {
+    constexpr int B = AsmRow<D>::B;
     AsmTable<D>& T = *S.tab;
     int j = T.n - 1;
 #pragma unroll 1
     for (; j >= 0; --j)       // newest first: a trajectory revisits the cell it just left
         if (T.key[j] == S.pkey) break;
-    if (j < 0) {
+    const bool fresh = j < 0;
+    if (fresh) {
         if (T.n == AsmTable<D>::CAP) {
             T.overflow = true;
             return;
         }
         j = T.n++;
         T.key[j] = S.pkey;
-#pragma unroll
-        for (int k = 0; k < (1 << D) * D; ++k) T.blk[j][k] = S.pblk[k];
-        return;
     }
+    float4* dst = reinterpret_cast<float4*>(S.blk + (size_t)j * S.stride);
 #pragma unroll
-    for (int k = 0; k < (1 << D) * D; ++k) T.blk[j][k] += S.pblk[k];
+    for (int k = 0; k < B / 4; ++k) {
+        float4 b = make_float4(S.pblk[4 * k], S.pblk[4 * k + 1], S.pblk[4 * k + 2], S.pblk[4 * k + 3]);
+        if (!fresh) {
+            const float4 o = dst[k];
+            b.x += o.x;
+            b.y += o.y;
+            b.z += o.z;
+            b.w += o.w;
+        }
+        dst[k] = b;
+    }
 }
 
 template <int D>
@@ -826,6 +840,39 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
     for (int a = 0; a < D; ++a) u[a] = fmaf(s6, acc[a] + vs[a], u[a]);
 }
 
+// Stage positions of step k from its start u (Alg. 1 without the final
+// update): rec = (u, u2, u3, u4), the same arithmetic as rk4_step, so the
+// positions equal those the forward sweep met.  Used by the adjoint sweep
+// when only the step starts were recorded.
+template <int D, bool NS, bool CACHE>
+__device__ __forceinline__ void rk4_positions(const TraceArgs& A, const float* V, const float* u, int k, float* rec,
+                                              CellCache<D, false>& C) {
+    size_t s1, s2, s4;
+    step_slices<NS>(A, k, s1, s2, s4);
+    Start<D> sv;
+    start_on_velocity<D>(A, sv);
+    const float dt = A.dt, hdt = 0.5f * A.dt;
+    int p[D];
+    float f[D], vs[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) rec[a] = u[a];
+    locate<D>(A.vg, sv, u, p, f);
+    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s1, p, f, C, vs);
+    else stage_value<D>(A.vg, V, s1, p, f, vs);
+#pragma unroll
+    for (int a = 0; a < D; ++a) rec[D + a] = fmaf(hdt, vs[a], u[a]);
+    locate<D>(A.vg, sv, rec + D, p, f);
+    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
+    else stage_value<D>(A.vg, V, s2, p, f, vs);
+#pragma unroll
+    for (int a = 0; a < D; ++a) rec[2 * D + a] = fmaf(hdt, vs[a], u[a]);
+    locate<D>(A.vg, sv, rec + 2 * D, p, f);
+    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
+    else stage_value<D>(A.vg, V, s2, p, f, vs);
+#pragma unroll
+    for (int a = 0; a < D; ++a) rec[3 * D + a] = fmaf(dt, vs[a], u[a]);
+}
+
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
 template <int D, bool NS, bool REC, bool CACHE>
@@ -946,9 +993,8 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float
     for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
 }
 
-// Store one assembled row entry-major: the key of entry e of voxel i at
-// [e][i], its block of 2^d corner vectors contiguous at [e][i][corner][q]
-// (96 bytes in 3D, 32 in 2D), so a warp streams one contiguous range per entry.
+// Finish one assembled row: its keys at [e][voxel] (the blocks are already
+// in place, [e][voxel][corner][q], written by asm_commit) and its length.
 template <int D>
 __device__ __forceinline__ void write_row(const TraceArgs& A, const AsmTable<D>& S, int vox) {
     const long long M = (long long)A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
@@ -958,15 +1004,8 @@ __device__ __forceinline__ void write_row(const TraceArgs& A, const AsmTable<D>&
         return;
     }
     A.ecnt[vox] = S.n;
-    constexpr int B = (1 << D) * D;
 #pragma unroll 1
-    for (int j = 0; j < S.n; ++j) {
-        A.ekey[j * M + vox] = S.key[j];
-        float4* dst = reinterpret_cast<float4*>(A.eblk + ((size_t)j * M + vox) * B);
-#pragma unroll
-        for (int k = 0; k < B / 4; ++k)
-            dst[k] = make_float4(S.blk[j][4 * k], S.blk[j][4 * k + 1], S.blk[j][4 * k + 2], S.blk[j][4 * k + 3]);
-    }
+    for (int j = 0; j < S.n; ++j) A.ekey[j * M + vox] = S.key[j];
 }
 
 // Products with the assembled J, one thread per voxel i (row i):
@@ -1127,7 +1166,18 @@ struct TraceOccupancy {
         MODE == MODE_FWD ? ((D == 3 && MODEL == LGNK_TRANSPORT) ? 3 : 4) : ((D == 3 && MODEL == LGNK_TRANSPORT) ? 2 : 3);
 };
 
-template <int D, bool NS, int MODEL, int MODE>
+// Dynamic shared memory of the tracing kernels: the stage-position records
+// of the forward sweep when they are kept on chip (REC 1 and 2 below).
+extern __shared__ float4 trace_rec_smem[];
+
+// Where the forward sweep leaves what the adjoint sweep reads back (REC):
+//   0  every step's four stage positions in a per-thread local array, one
+//      16-byte word per float4 (local memory: large N)
+//   1  the same words in shared memory, [step][word][thread] (conflict-free
+//      16-byte accesses)
+//   2  only each step's start in shared memory, [step][thread]; the adjoint
+//      recomputes the other three stage positions from it (rk4_positions)
+template <int D, bool NS, int MODEL, int MODE, int REC>
 __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::value)) trace_kernel(const TraceArgs A) {
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
@@ -1150,11 +1200,15 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
 
     SC S;
     scatter_init<D>(S, A.G);
-    AsmTable<D> row_table;        // MODE_ASM: the row being assembled
+    AsmTable<D> row_table;        // MODE_ASM: the keys of the row being assembled
     if constexpr (MODE == MODE_ASM) {
         row_table.n = 0;
         row_table.overflow = false;
         S.tab = &row_table;
+        const size_t Mi = (size_t)A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
+        const int vx = idx[0] + A.ig.m[0] * (idx[1] + A.ig.m[1] * (D == 3 ? idx[2] : 0));
+        S.stride = Mi * AsmRow<D>::B;
+        S.blk = A.eblk + (size_t)vx * AsmRow<D>::B;
     }
 
     if (active) {
@@ -1170,13 +1224,24 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
         CellCache<D, false> vcache;   // v corners for the forward and adjoint sweeps
         vcache.key = -1;
         // stage positions of every step (recorded for the adjoint sweep)
-        float hist[ADJOINT ? LGNK_MAX_STEPS : 1][4 * D];
+        constexpr bool FULL = ADJOINT && REC != 2;
+        float4 lrec[(ADJOINT && REC == 0) ? LGNK_MAX_STEPS * D : 1];
+        const int bd = blockDim.x, tid = threadIdx.x;
 
 #pragma unroll 1
         for (int k = 0; k < A.N; ++k) {
-            float* rec = hist[ADJOINT ? k : 0];
-            if (TANGENT) rk4_tangent_step<D, NS, ADJOINT, CACHE>(A, V, dV, u, dy, k, rec, tcache);
-            else rk4_step<D, NS, ADJOINT, CACHE>(A, V, u, k, rec, vcache);
+            float rec[4 * D];
+            if constexpr (ADJOINT && REC == 2) trace_rec_smem[k * bd + tid] = make_float4(u[0], u[1], D == 3 ? u[2] : 0.0f, 0.0f);
+            if (TANGENT) rk4_tangent_step<D, NS, FULL, CACHE>(A, V, dV, u, dy, k, rec, tcache);
+            else rk4_step<D, NS, FULL, CACHE>(A, V, u, k, rec, vcache);
+            if constexpr (FULL) {
+#pragma unroll
+                for (int w = 0; w < D; ++w) {
+                    const float4 word = make_float4(rec[4 * w], rec[4 * w + 1], rec[4 * w + 2], rec[4 * w + 3]);
+                    if constexpr (REC == 0) lrec[k * D + w] = word;
+                    else trace_rec_smem[(k * D + w) * bd + tid] = word;
+                }
+            }
         }
         if (A.yout != nullptr) {
             const int M = A.ig.m[0] * A.ig.m[1] * (D == 3 ? A.ig.m[2] : 1);
@@ -1260,8 +1325,24 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
 
         if (ADJOINT) {
 #pragma unroll 1
-            for (int k = A.N - 1; k >= 0; --k)
-                rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, hist[ADJOINT ? k : 0], lam, k, vcache);
+            for (int k = A.N - 1; k >= 0; --k) {
+                float rec[4 * D];
+                if constexpr (REC == 2) {
+                    const float4 w0 = trace_rec_smem[k * bd + tid];
+                    const float u0[3] = {w0.x, w0.y, w0.z};
+                    rk4_positions<D, NS, CACHE>(A, V, u0, k, rec, vcache);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < D; ++w) {
+                        const float4 word = REC == 0 ? lrec[k * D + w] : trace_rec_smem[(k * D + w) * bd + tid];
+                        rec[4 * w] = word.x;
+                        rec[4 * w + 1] = word.y;
+                        rec[4 * w + 2] = word.z;
+                        rec[4 * w + 3] = word.w;
+                    }
+                }
+                rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, rec, lam, k, vcache);
+            }
             scatter_finish<D>(A.vg, S);
             if constexpr (MODE == MODE_ASM) {
                 write_row<D>(A, *S.tab, vox);
@@ -1285,7 +1366,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
     }
 }
 
-template <int D, bool NS, int MODEL, int MODE>
+template <int D, bool NS, int MODEL, int MODE, int REC>
 static cudaError_t launch_one(const TraceArgs& a0, int nblocks, cudaStream_t s) {
     (void)nblocks;
     TraceArgs a = a0;
@@ -1294,26 +1375,48 @@ static cudaError_t launch_one(const TraceArgs& a0, int nblocks, cudaStream_t s) 
     for (int i = 0; i < 3; ++i) a.tiles[i] = (a.ig.m[i] + ts[i] - 1) / ts[i];
     const int blocks = a.tiles[0] * a.tiles[1] * a.tiles[2];
     const int threads = ts[0] * ts[1] * ts[2];
-    trace_kernel<D, NS, MODEL, MODE><<<blocks, threads, 0, s>>>(a);
+    const size_t smem = trace_record_smem(D, REC, a.N);
+    if (smem > (48u << 10)) {
+        // above the default limit a kernel opts in to the device's per-CTA maximum
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        if (smem > (size_t)optin) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(trace_kernel<D, NS, MODEL, MODE, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin);
+        if (e != cudaSuccess) return e;
+    }
+    trace_kernel<D, NS, MODEL, MODE, REC><<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int D, bool NS, int MODEL, int MODE>
+static cudaError_t launch_rec(const TraceArgs& a, int nblocks, cudaStream_t s) {
+    switch (a.rec) {
+        case 0: return launch_one<D, NS, MODEL, MODE, 0>(a, nblocks, s);
+        case 1: return launch_one<D, NS, MODEL, MODE, 1>(a, nblocks, s);
+        case 2: return launch_one<D, NS, MODEL, MODE, 2>(a, nblocks, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int D, bool NS>
 static cudaError_t launch_dim(int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s) {
     if (model == LGNK_TRANSPORT) {
         switch (mode) {
-            case MODE_FWD: return launch_one<D, NS, LGNK_TRANSPORT, MODE_FWD>(a, nblocks, s);
-            case MODE_JVP: return launch_one<D, NS, LGNK_TRANSPORT, MODE_JVP>(a, nblocks, s);
-            case MODE_JTVP: return launch_one<D, NS, LGNK_TRANSPORT, MODE_JTVP>(a, nblocks, s);
-            case MODE_HESS: return launch_one<D, NS, LGNK_TRANSPORT, MODE_HESS>(a, nblocks, s);
-            case MODE_OBJGRAD: return launch_one<D, NS, LGNK_TRANSPORT, MODE_OBJGRAD>(a, nblocks, s);
-            case MODE_ASM: return launch_one<D, NS, LGNK_TRANSPORT, MODE_ASM>(a, nblocks, s);
+            case MODE_FWD: return launch_one<D, NS, LGNK_TRANSPORT, MODE_FWD, 0>(a, nblocks, s);
+            case MODE_JVP: return launch_one<D, NS, LGNK_TRANSPORT, MODE_JVP, 0>(a, nblocks, s);
+            case MODE_JTVP: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_JTVP>(a, nblocks, s);
+            case MODE_HESS: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_HESS>(a, nblocks, s);
+            case MODE_OBJGRAD: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_OBJGRAD>(a, nblocks, s);
+            case MODE_ASM: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_ASM>(a, nblocks, s);
         }
     } else {
         switch (mode) {
-            case MODE_FWD: return launch_one<D, NS, LGNK_CONTINUITY, MODE_FWD>(a, nblocks, s);
-            case MODE_JVP: return launch_one<D, NS, LGNK_CONTINUITY, MODE_JVP>(a, nblocks, s);
-            case MODE_JTVP: return launch_one<D, NS, LGNK_CONTINUITY, MODE_JTVP>(a, nblocks, s);
+            case MODE_FWD: return launch_one<D, NS, LGNK_CONTINUITY, MODE_FWD, 0>(a, nblocks, s);
+            case MODE_JVP: return launch_one<D, NS, LGNK_CONTINUITY, MODE_JVP, 0>(a, nblocks, s);
+            case MODE_JTVP: return launch_rec<D, NS, LGNK_CONTINUITY, MODE_JTVP>(a, nblocks, s);
         }
     }
     return cudaErrorInvalidValue;
