@@ -305,9 +305,7 @@ int trace_blocks_for(const lgnk_ctx* ctx, int mode) {
     return n;
 }
 
-lgnk_status trace(lgnk_ctx* ctx, int mode, const TraceArgs& a0) {
-    TraceArgs a = a0;
-    a.rec = trace_record_mode(ctx->d, ctx->prob.model, mode, ctx->N);
+lgnk_status trace(lgnk_ctx* ctx, int mode, const TraceArgs& a) {
     if (ctx->prof) TRY(record_event(ctx));
     KL(launch_trace(ctx->d, ctx->K > 1, ctx->prob.model, mode, a, ctx->trace_blocks, ctx->stream));
     ctx->trace_launches++;

@@ -73,35 +73,7 @@ struct TraceArgs {
     int* eflag;               // set to 1 when a row needs more than ewidth entries
     double* cpartial;         // per-block sums of the entries per row (may be NULL)
     int ewidth;               // entries per voxel the arrays hold
-    int rec;                  // where the adjoint modes keep the stage positions (trace_record_mode)
 };
-
-// Where a tracing launch keeps the forward sweep's stage positions for its
-// adjoint sweep: 0 every step's four positions in local memory, 1 the same in
-// shared memory, 2 each step's start in shared memory (the adjoint recomputes
-// the other positions).  Shared memory is chosen while the CTAs per SM the
-// kernel runs at still fit: the full record while N is small, the starts
-// (a quarter of it, at the cost of three stage evaluations per step) for
-// longer trajectories, local memory beyond that.
-inline size_t trace_record_smem(int d, int rec, int N) {
-    return rec == 1 ? (size_t)N * d * 16 * LGNK_BLOCK : rec == 2 ? (size_t)N * 16 * LGNK_BLOCK : 0;
-}
-inline int trace_record_mode(int d, int model, int mode, int N) {
-    const bool adjoint = mode == MODE_JTVP || mode == MODE_HESS || mode == MODE_OBJGRAD || mode == MODE_ASM;
-    if (!adjoint) return 0;
-#ifdef LGNK_REC_FORCE
-    // build option: one record mode wherever it fits (measurements of the modes)
-    if (LGNK_REC_FORCE == 0 || (size_t)3 * trace_record_smem(d, LGNK_REC_FORCE, N) <= (216u << 10)) return LGNK_REC_FORCE;
-#endif
-    // CTAs per SM of the adjoint kernels (TraceOccupancy in trace_impl.cuh)
-    // and the shared memory of an SM they may fill (of its 228 KB, leaving
-    // room for the per-CTA reserve and the reductions' static arrays)
-    const int ctas = (d == 3 && model == LGNK_TRANSPORT) ? 2 : 3;
-    const size_t budget = 216u << 10;
-    if (model == LGNK_TRANSPORT && (size_t)ctas * trace_record_smem(d, 1, N) <= budget) return 1;
-    if ((size_t)ctas * trace_record_smem(d, 2, N) <= budget) return 2;
-    return 0;
-}
 
 // Assembled J (transport): at most this many (slice, cell) blocks per row.
 inline int asm_capacity(int d) { return d == 3 ? 16 : 32; }

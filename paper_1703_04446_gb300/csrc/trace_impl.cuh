@@ -670,6 +670,10 @@ __device__ __forceinline__ float sample_image(const DevGrid& g, const Start<D>& 
 }
 
 // acc += mass * w(y) (push-forward, Eq. 7) or mass * (grad_y w(y) . dp).
+// Pairing x-neighbouring lanes whose cells are adjacent (one shuffle per
+// shared corner, half the x = 0 corners' atomics skipped) measured no change
+// on the brain-scale forward and JVP (1.936 / 3.854 ms against 1.931 / 3.866
+// ms), so every corner takes its own atomic.
 template <int D, bool TANGENT>
 __device__ __forceinline__ void splat_image(const DevGrid& g, const Start<D>& s, float* acc, const float* u,
                                             float mass, const float* dp) {
@@ -838,39 +842,6 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
     const float s6 = dt / 6.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) u[a] = fmaf(s6, acc[a] + vs[a], u[a]);
-}
-
-// Stage positions of step k from its start u (Alg. 1 without the final
-// update): rec = (u, u2, u3, u4), the same arithmetic as rk4_step, so the
-// positions equal those the forward sweep met.  Used by the adjoint sweep
-// when only the step starts were recorded.
-template <int D, bool NS, bool CACHE>
-__device__ __forceinline__ void rk4_positions(const TraceArgs& A, const float* V, const float* u, int k, float* rec,
-                                              CellCache<D, false>& C) {
-    size_t s1, s2, s4;
-    step_slices<NS>(A, k, s1, s2, s4);
-    Start<D> sv;
-    start_on_velocity<D>(A, sv);
-    const float dt = A.dt, hdt = 0.5f * A.dt;
-    int p[D];
-    float f[D], vs[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) rec[a] = u[a];
-    locate<D>(A.vg, sv, u, p, f);
-    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s1, p, f, C, vs);
-    else stage_value<D>(A.vg, V, s1, p, f, vs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) rec[D + a] = fmaf(hdt, vs[a], u[a]);
-    locate<D>(A.vg, sv, rec + D, p, f);
-    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
-    else stage_value<D>(A.vg, V, s2, p, f, vs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) rec[2 * D + a] = fmaf(hdt, vs[a], u[a]);
-    locate<D>(A.vg, sv, rec + 2 * D, p, f);
-    if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
-    else stage_value<D>(A.vg, V, s2, p, f, vs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) rec[3 * D + a] = fmaf(dt, vs[a], u[a]);
 }
 
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
@@ -1166,18 +1137,7 @@ struct TraceOccupancy {
         MODE == MODE_FWD ? ((D == 3 && MODEL == LGNK_TRANSPORT) ? 3 : 4) : ((D == 3 && MODEL == LGNK_TRANSPORT) ? 2 : 3);
 };
 
-// Dynamic shared memory of the tracing kernels: the stage-position records
-// of the forward sweep when they are kept on chip (REC 1 and 2 below).
-extern __shared__ float4 trace_rec_smem[];
-
-// Where the forward sweep leaves what the adjoint sweep reads back (REC):
-//   0  every step's four stage positions in a per-thread local array, one
-//      16-byte word per float4 (local memory: large N)
-//   1  the same words in shared memory, [step][word][thread] (conflict-free
-//      16-byte accesses)
-//   2  only each step's start in shared memory, [step][thread]; the adjoint
-//      recomputes the other three stage positions from it (rk4_positions)
-template <int D, bool NS, int MODEL, int MODE, int REC>
+template <int D, bool NS, int MODEL, int MODE>
 __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::value)) trace_kernel(const TraceArgs A) {
     using VT = typename VecT<D>::type;
     constexpr bool TANGENT = (MODE == MODE_JVP || MODE == MODE_HESS);
@@ -1223,24 +1183,24 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
         tcache.key = -1;
         CellCache<D, false> vcache;   // v corners for the forward and adjoint sweeps
         vcache.key = -1;
-        // stage positions of every step (recorded for the adjoint sweep)
-        constexpr bool FULL = ADJOINT && REC != 2;
-        float4 lrec[(ADJOINT && REC == 0) ? LGNK_MAX_STEPS * D : 1];
-        const int bd = blockDim.x, tid = threadIdx.x;
+        // stage positions of every step, recorded for the adjoint sweep in a
+        // per-thread local array as 16-byte words (4D floats per step).  Kept
+        // in shared memory instead, the full record (2 CTAs x 96 KB on the
+        // 128^3 matvec) shrank the L1 that the gathers use and measured slower
+        // (0.828 against 0.814 ms); keeping only each step's start there and
+        // recomputing the other positions in the adjoint sweep measured 0.974
+        // ms, and on the brain-scale mass-preserving J^T 9.56 against 8.47 ms.
+        float4 lrec[ADJOINT ? LGNK_MAX_STEPS * D : 1];
 
 #pragma unroll 1
         for (int k = 0; k < A.N; ++k) {
             float rec[4 * D];
-            if constexpr (ADJOINT && REC == 2) trace_rec_smem[k * bd + tid] = make_float4(u[0], u[1], D == 3 ? u[2] : 0.0f, 0.0f);
-            if (TANGENT) rk4_tangent_step<D, NS, FULL, CACHE>(A, V, dV, u, dy, k, rec, tcache);
-            else rk4_step<D, NS, FULL, CACHE>(A, V, u, k, rec, vcache);
-            if constexpr (FULL) {
+            if (TANGENT) rk4_tangent_step<D, NS, ADJOINT, CACHE>(A, V, dV, u, dy, k, rec, tcache);
+            else rk4_step<D, NS, ADJOINT, CACHE>(A, V, u, k, rec, vcache);
+            if constexpr (ADJOINT) {
 #pragma unroll
-                for (int w = 0; w < D; ++w) {
-                    const float4 word = make_float4(rec[4 * w], rec[4 * w + 1], rec[4 * w + 2], rec[4 * w + 3]);
-                    if constexpr (REC == 0) lrec[k * D + w] = word;
-                    else trace_rec_smem[(k * D + w) * bd + tid] = word;
-                }
+                for (int w = 0; w < D; ++w)
+                    lrec[k * D + w] = make_float4(rec[4 * w], rec[4 * w + 1], rec[4 * w + 2], rec[4 * w + 3]);
             }
         }
         if (A.yout != nullptr) {
@@ -1327,19 +1287,13 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
 #pragma unroll 1
             for (int k = A.N - 1; k >= 0; --k) {
                 float rec[4 * D];
-                if constexpr (REC == 2) {
-                    const float4 w0 = trace_rec_smem[k * bd + tid];
-                    const float u0[3] = {w0.x, w0.y, w0.z};
-                    rk4_positions<D, NS, CACHE>(A, V, u0, k, rec, vcache);
-                } else {
 #pragma unroll
-                    for (int w = 0; w < D; ++w) {
-                        const float4 word = REC == 0 ? lrec[k * D + w] : trace_rec_smem[(k * D + w) * bd + tid];
-                        rec[4 * w] = word.x;
-                        rec[4 * w + 1] = word.y;
-                        rec[4 * w + 2] = word.z;
-                        rec[4 * w + 3] = word.w;
-                    }
+                for (int w = 0; w < D; ++w) {
+                    const float4 word = lrec[k * D + w];
+                    rec[4 * w] = word.x;
+                    rec[4 * w + 1] = word.y;
+                    rec[4 * w + 2] = word.z;
+                    rec[4 * w + 3] = word.w;
                 }
                 rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, rec, lam, k, vcache);
             }
@@ -1366,7 +1320,7 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
     }
 }
 
-template <int D, bool NS, int MODEL, int MODE, int REC>
+template <int D, bool NS, int MODEL, int MODE>
 static cudaError_t launch_one(const TraceArgs& a0, int nblocks, cudaStream_t s) {
     (void)nblocks;
     TraceArgs a = a0;
@@ -1375,48 +1329,26 @@ static cudaError_t launch_one(const TraceArgs& a0, int nblocks, cudaStream_t s) 
     for (int i = 0; i < 3; ++i) a.tiles[i] = (a.ig.m[i] + ts[i] - 1) / ts[i];
     const int blocks = a.tiles[0] * a.tiles[1] * a.tiles[2];
     const int threads = ts[0] * ts[1] * ts[2];
-    const size_t smem = trace_record_smem(D, REC, a.N);
-    if (smem > (48u << 10)) {
-        // above the default limit a kernel opts in to the device's per-CTA maximum
-        int dev = 0, optin = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e != cudaSuccess) return e;
-        if (smem > (size_t)optin) return cudaErrorInvalidValue;
-        e = cudaFuncSetAttribute(trace_kernel<D, NS, MODEL, MODE, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 optin);
-        if (e != cudaSuccess) return e;
-    }
-    trace_kernel<D, NS, MODEL, MODE, REC><<<blocks, threads, smem, s>>>(a);
+    trace_kernel<D, NS, MODEL, MODE><<<blocks, threads, 0, s>>>(a);
     return cudaGetLastError();
-}
-
-template <int D, bool NS, int MODEL, int MODE>
-static cudaError_t launch_rec(const TraceArgs& a, int nblocks, cudaStream_t s) {
-    switch (a.rec) {
-        case 0: return launch_one<D, NS, MODEL, MODE, 0>(a, nblocks, s);
-        case 1: return launch_one<D, NS, MODEL, MODE, 1>(a, nblocks, s);
-        case 2: return launch_one<D, NS, MODEL, MODE, 2>(a, nblocks, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 template <int D, bool NS>
 static cudaError_t launch_dim(int model, int mode, const TraceArgs& a, int nblocks, cudaStream_t s) {
     if (model == LGNK_TRANSPORT) {
         switch (mode) {
-            case MODE_FWD: return launch_one<D, NS, LGNK_TRANSPORT, MODE_FWD, 0>(a, nblocks, s);
-            case MODE_JVP: return launch_one<D, NS, LGNK_TRANSPORT, MODE_JVP, 0>(a, nblocks, s);
-            case MODE_JTVP: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_JTVP>(a, nblocks, s);
-            case MODE_HESS: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_HESS>(a, nblocks, s);
-            case MODE_OBJGRAD: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_OBJGRAD>(a, nblocks, s);
-            case MODE_ASM: return launch_rec<D, NS, LGNK_TRANSPORT, MODE_ASM>(a, nblocks, s);
+            case MODE_FWD: return launch_one<D, NS, LGNK_TRANSPORT, MODE_FWD>(a, nblocks, s);
+            case MODE_JVP: return launch_one<D, NS, LGNK_TRANSPORT, MODE_JVP>(a, nblocks, s);
+            case MODE_JTVP: return launch_one<D, NS, LGNK_TRANSPORT, MODE_JTVP>(a, nblocks, s);
+            case MODE_HESS: return launch_one<D, NS, LGNK_TRANSPORT, MODE_HESS>(a, nblocks, s);
+            case MODE_OBJGRAD: return launch_one<D, NS, LGNK_TRANSPORT, MODE_OBJGRAD>(a, nblocks, s);
+            case MODE_ASM: return launch_one<D, NS, LGNK_TRANSPORT, MODE_ASM>(a, nblocks, s);
         }
     } else {
         switch (mode) {
-            case MODE_FWD: return launch_one<D, NS, LGNK_CONTINUITY, MODE_FWD, 0>(a, nblocks, s);
-            case MODE_JVP: return launch_one<D, NS, LGNK_CONTINUITY, MODE_JVP, 0>(a, nblocks, s);
-            case MODE_JTVP: return launch_rec<D, NS, LGNK_CONTINUITY, MODE_JTVP>(a, nblocks, s);
+            case MODE_FWD: return launch_one<D, NS, LGNK_CONTINUITY, MODE_FWD>(a, nblocks, s);
+            case MODE_JVP: return launch_one<D, NS, LGNK_CONTINUITY, MODE_JVP>(a, nblocks, s);
+            case MODE_JTVP: return launch_one<D, NS, LGNK_CONTINUITY, MODE_JTVP>(a, nblocks, s);
         }
     }
     return cudaErrorInvalidValue;

@@ -14,7 +14,7 @@ import torch
 
 from oracle import lagrangian as L
 from oracle.objective import Problem as OP, gradient, hessvec, objective
-from oracle.solver import apply_preconditioner, gauss_newton
+from oracle.solver import apply_preconditioner, armijo, gauss_newton, pcg
 from paper_1703_04446_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -38,12 +38,16 @@ def _setup(name, seed=0):
 def test_transport_64_iterates_follow_the_oracle(matvec):
     """2D intensity-preserving workload (64^2, 10 GN / 20 PCG): every GN step
     from the GPU's own iterate, with the assembled J and matrix-free.  The
-    step is compared twice: against the oracle's own PCG step (when both took
-    the same number of CG iterations, to 1e-2: the k-th CG iterate amplifies
-    the FP32 rounding of its inputs by up to the condition number of the
-    preconditioned system on the Krylov space), and through the oracle's
-    operator, where it must meet the PCG stopping test |H x + g| <= 0.1 |g|
-    (5% slack for the FP32 recurrence) unless PCG hit its cap."""
+    step is compared twice: against the oracle's step after the same number
+    of CG iterations (when the two residual norms cross the 0.1 threshold one
+    iteration apart, the oracle is run for the GPU's count), in the norm of
+    the Gauss-Newton Hessian H that CG minimises its error in, to 1e-2 (the
+    k-th CG iterate amplifies the FP32 rounding of its inputs most along
+    directions of small curvature, which this norm weighs least; in the plain
+    norm late iterates differ by a few percent), and through
+    the oracle's operator, where it must meet the PCG stopping test
+    |H x + g| <= 0.1 |g| (5% slack for the FP32 recurrence) unless PCG hit
+    its cap.  The objective after the step then matches to 1e-4."""
     ctx, op, T64, R64, tT, tR = _setup("2d_transport_64")
     v = torch.zeros(op.vshape, device="cuda")
     g_first = None
@@ -57,10 +61,20 @@ def test_transport_64_iterates_follow_the_oracle(matvec):
         step = v_next.cpu().numpy().astype(np.float64) - v64
         x = step / rep["last_mu"] if rep["last_mu"] > 0 else step
         res = float(np.linalg.norm(hessvec(op, v64, T64, x) + g) / np.linalg.norm(g))
+        ref_step, J_after, mu_o = h["mu"] * h["dv"], repo["J"], h["mu"]
+        if rep["pcg_iters"] != h["pcg"]:
+            # the two residual norms crossed the 0.1 threshold one iteration
+            # apart: the oracle's step after the GPU's number of CG iterations
+            dv, _, _ = pcg(lambda q: hessvec(op, v64, T64, q), -g, lambda r: apply_preconditioner(op, r), tol=0.0,
+                           maxit=rep["pcg_iters"])
+            mu_o, J_after = armijo(lambda w: objective(op, w, T64, R64)[0], v64, h["J"], g, dv)
+            ref_step = mu_o * dv
+        e = step - ref_step
+        stepH = float(np.sqrt(np.sum(e * hessvec(op, v64, T64, e)) / np.sum(ref_step * hessvec(op, v64, T64, ref_step))))
         rows.append(dict(k=k, J0=abs(rep["J0"] - h["J"]) / h["J"], g0=abs(rep["g0"] - h["g"]) / h["g"],
-                         pcg=(rep["pcg_iters"], h["pcg"]), mu=(rep["last_mu"], h["mu"]),
-                         step=float(np.linalg.norm(step - h["mu"] * h["dv"]) / np.linalg.norm(h["mu"] * h["dv"])),
-                         res=res, J=abs(rep["J"] - repo["J"]) / repo["J"]))
+                         pcg=(rep["pcg_iters"], h["pcg"]), mu=(rep["last_mu"], mu_o),
+                         step=float(np.linalg.norm(e) / np.linalg.norm(ref_step)), stepH=stepH,
+                         res=res, J=abs(rep["J"] - J_after) / J_after))
         g_first = g_first or h["g"]
         v = v_next
         if h["g"] <= 1e-3 * g_first:
@@ -69,8 +83,7 @@ def test_transport_64_iterates_follow_the_oracle(matvec):
     for r in rows:
         assert r["J0"] <= 1e-5 and r["g0"] <= 1e-5, r
         assert abs(r["pcg"][0] - r["pcg"][1]) <= 1, r
-        if r["pcg"][0] == r["pcg"][1]:
-            assert r["step"] <= 1e-2, r
+        assert r["stepH"] <= 1e-2 and r["step"] <= 1e-1, r
         if r["pcg"][0] < 20:
             assert r["res"] <= 0.1 * 1.05, r
         assert r["mu"][0] == r["mu"][1], r
