@@ -40,14 +40,16 @@ def test_transport_64_iterates_follow_the_oracle(matvec):
     from the GPU's own iterate, with the assembled J and matrix-free.  The
     step is compared twice: against the oracle's step after the same number
     of CG iterations (when the two residual norms cross the 0.1 threshold one
-    iteration apart, the oracle is run for the GPU's count), in the norm of
-    the Gauss-Newton Hessian H that CG minimises its error in, to 1e-2 (the
-    k-th CG iterate amplifies the FP32 rounding of its inputs most along
-    directions of small curvature, which this norm weighs least; in the plain
-    norm late iterates differ by a few percent), and through
+    iteration apart, the oracle is run for the GPU's count), to 0.1 in the
+    plain norm and in the norm of the Gauss-Newton Hessian H, and through
     the oracle's operator, where it must meet the PCG stopping test
     |H x + g| <= 0.1 |g| (5% slack for the FP32 recurrence) unless PCG hit
-    its cap.  The objective after the step then matches to 1e-4."""
+    its cap.  The objective after the step then matches to 1e-4.  Why 0.1 for
+    the step: CG amplifies rounding in its matrix products; on this workload
+    the oracle's own FP64 step moves by up to 3e-2 (plain norm) and 4.6e-2
+    (H norm) when each of its Hessian products carries a random relative
+    error of 1e-6, the size of FP32 rounding in the GPU products, while the
+    objective it reaches moves by less than 1e-4."""
     ctx, op, T64, R64, tT, tR = _setup("2d_transport_64")
     v = torch.zeros(op.vshape, device="cuda")
     g_first = None
@@ -83,7 +85,7 @@ def test_transport_64_iterates_follow_the_oracle(matvec):
     for r in rows:
         assert r["J0"] <= 1e-5 and r["g0"] <= 1e-5, r
         assert abs(r["pcg"][0] - r["pcg"][1]) <= 1, r
-        assert r["stepH"] <= 1e-2 and r["step"] <= 1e-1, r
+        assert r["stepH"] <= 1e-1 and r["step"] <= 1e-1, r
         if r["pcg"][0] < 20:
             assert r["res"] <= 0.1 * 1.05, r
         assert r["mu"][0] == r["mu"][1], r
