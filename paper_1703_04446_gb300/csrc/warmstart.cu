@@ -15,160 +15,66 @@
 // the convolution's input indexing.  Weights are used as bfloat16 (rounded from
 // FP32 master weights after every Adam step); activations, gradients and
 // accumulation are FP32.  Loss 1/2 mean((v - target)^2) / scale^2.
+//
+// Every convolution, its data gradient and its weight gradient run as implicit
+// GEMMs on the tensor cores (conv_umma.cuh); bias gradients, the loss, the
+// ReLU masks and Adam are elementwise kernels here.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <new>
 #include <vector>
 
+#include "conv_umma.cuh"
 #include "lgnk_internal.h"
 
 namespace {
 
 constexpr int kT = 256;
-constexpr int kCo = 8;     // output channels per forward CTA
-constexpr int kCiChunk = 32;
-constexpr int kMaxSlices = 64;   // pixel slices of the weight-gradient reduction
+constexpr int kMaxSlices = 64;   // K slices of the weight-gradient GEMM (partials summed in order)
 
 struct Layer {
     int ci, co, stride, up;   // input channels, output channels, stride, input upsampled
     int hin, hout;            // input and output side lengths (square)
     size_t woff, boff;        // offsets of W and b in the parameter vector
+    // bf16 weight matrices of the tensor-core GEMMs, zero padded, K ordered
+    // as the operand planes are (channel fastest):
+    // forward wf[co][tap * cpi + ci] (cpi = ci rounded up to 8; rows to a
+    // multiple of bnf, rows of ldf), data gradient
+    // wd[ci][(tap * R + up position) * cpo + co] (cpo = co rounded up to 8, R = 4 when up)
+    int cpi, cpo, bnf, ldf, rowsf, bnd, ldd, rowsd;
+    __nv_bfloat16 *wf, *wd;
 };
 
-// Input value at effective position (y, x) of an (optionally upsampled) input
-// of side hin; zero outside.
-__device__ __forceinline__ float in_eff(const float* __restrict__ in, int hin, int up, int y, int x) {
-    const int he = up ? 2 * hin : hin;
-    if (y < 0 || x < 0 || y >= he || x >= he) return 0.0f;
-    if (up) {
-        y >>= 1;
-        x >>= 1;
-    }
-    return __ldg(in + (size_t)y * hin + x);
-}
+#ifndef LGNK_CONV_STAGES
+#define LGNK_CONV_STAGES 1    // operand buffers per CTA (1: two CTAs per SM)
+#endif
 
-// out[b][co][oy][ox] = act(bias + sum_ci,k W[co][ci][k] in_eff[b][ci][oy s + ky - 1][ox s + kx - 1])
-// act: relu when relu != 0; r (optional) receives the activation, out = act + add
-// (optional skip tensor); the result is multiplied by `scale`.
-__global__ void __launch_bounds__(kT) conv_fwd_kernel(const float* __restrict__ in, const __nv_bfloat16* __restrict__ W,
-                                                      const float* __restrict__ bias, float* out, float* r,
-                                                      const float* __restrict__ add, Layer L, int relu, float scale) {
-    __shared__ float ws[kCo][kCiChunk][9];
-    const int tiles = (L.hout + 15) / 16;
-    const int tx = blockIdx.x % tiles, ty = blockIdx.x / tiles;
-    const int co0 = blockIdx.y * kCo;
-    const int b = blockIdx.z;
-    const int ox = tx * 16 + (threadIdx.x & 15), oy = ty * 16 + (threadIdx.x >> 4);
-    const bool active = ox < L.hout && oy < L.hout;
-    float acc[kCo];
-#pragma unroll
-    for (int k = 0; k < kCo; ++k) acc[k] = 0.0f;
-    const float* inb = in + (size_t)b * L.ci * L.hin * L.hin;
-    for (int c0 = 0; c0 < L.ci; c0 += kCiChunk) {
-        const int nc = min(kCiChunk, L.ci - c0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kCo * kCiChunk * 9; i += kT) {
-            const int co = i / (kCiChunk * 9), rem = i % (kCiChunk * 9), ci = rem / 9, k = rem % 9;
-            float w = 0.0f;
-            if (co0 + co < L.co && ci < nc) w = __bfloat162float(W[((size_t)(co0 + co) * L.ci + c0 + ci) * 9 + k]);
-            ws[co][ci][k] = w;
-        }
-        __syncthreads();
-        if (active) {
-            for (int ci = 0; ci < nc; ++ci) {
-                const float* inc = inb + (size_t)(c0 + ci) * L.hin * L.hin;
-                float v[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    v[k] = in_eff(inc, L.hin, L.up, oy * L.stride + k / 3 - 1, ox * L.stride + k % 3 - 1);
-#pragma unroll
-                for (int co = 0; co < kCo; ++co) {
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) acc[co] = fmaf(ws[co][ci][k], v[k], acc[co]);
-                }
-            }
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// The GEMMs' weight matrices from the FP32 master weights (bf16, nearest).
+__global__ void pack_wmats_kernel(const float* __restrict__ p, Layer L) {
+    const size_t nf = (size_t)L.rowsf * L.ldf, nd = (size_t)L.rowsd * L.ldd;
+    const int R = L.up ? 4 : 1;
+    const float* W = p + L.woff;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nf + nd; i += (size_t)gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        if (i < nf) {
+            const int n = (int)(i / L.ldf), k = (int)(i % L.ldf);
+            const int t = k / L.cpi, c = k - t * L.cpi;
+            if (n < L.co && t < 9 && c < L.ci) v = W[((size_t)n * L.ci + c) * 9 + t];
+            L.wf[i] = __float2bfloat16_rn(v);
+        } else {
+            const size_t j = i - nf;
+            const int n = (int)(j / L.ldd), k = (int)(j % L.ldd);
+            const int pos = k / L.cpo, cc = k - pos * L.cpo, t = pos / R;
+            if (n < L.ci && t < 9 && cc < L.co) v = W[((size_t)cc * L.ci + n) * 9 + t];
+            L.wd[j] = __float2bfloat16_rn(v);
         }
     }
-    if (!active) return;
-    for (int co = 0; co < kCo && co0 + co < L.co; ++co) {
-        float z = acc[co] + bias[co0 + co];
-        if (relu) z = fmaxf(z, 0.0f);
-        const size_t o = (((size_t)b * L.co + co0 + co) * L.hout + oy) * L.hout + ox;
-        if (r != nullptr) r[o] = z;
-        if (add != nullptr) z += add[o];
-        out[o] = scale * z;
-    }
-}
-
-// din[b][ci][y][x] (+)= sum over the effective positions the input (y, x) feeds
-// (four when upsampled) of sum_co,k W[co][ci][k] dz[b][co][oy][ox], where the
-// effective position e = o s + k - 1.
-__global__ void __launch_bounds__(kT) conv_bwd_data_kernel(const float* __restrict__ dz,
-                                                           const __nv_bfloat16* __restrict__ W, float* din, Layer L,
-                                                           int accumulate) {
-    const int b = blockIdx.z;
-    const int ci = blockIdx.y;
-    const size_t n = (size_t)L.hin * L.hin;
-    const float* dzb = dz + (size_t)b * L.co * L.hout * L.hout;
-    for (size_t i = blockIdx.x * (size_t)kT + threadIdx.x; i < n; i += (size_t)gridDim.x * kT) {
-        const int x = (int)(i % L.hin), y = (int)(i / L.hin);
-        float acc = 0.0f;
-        const int reps = L.up ? 2 : 1;
-        for (int dyy = 0; dyy < reps; ++dyy) {
-            for (int dxx = 0; dxx < reps; ++dxx) {
-                const int ey = L.up ? 2 * y + dyy : y, ex = L.up ? 2 * x + dxx : x;
-                for (int k = 0; k < 9; ++k) {
-                    const int ny = ey + 1 - k / 3, nx = ex + 1 - k % 3;
-                    if (ny < 0 || nx < 0) continue;
-                    if (L.stride == 2 && ((ny & 1) || (nx & 1))) continue;
-                    const int oy = ny / L.stride, ox = nx / L.stride;
-                    if (oy >= L.hout || ox >= L.hout) continue;
-                    const float* dzp = dzb + (size_t)oy * L.hout + ox;
-                    const __nv_bfloat16* wp = W + (size_t)ci * 9 + k;
-                    for (int co = 0; co < L.co; ++co)
-                        acc = fmaf(__bfloat162float(wp[(size_t)co * L.ci * 9]), __ldg(dzp + (size_t)co * L.hout * L.hout),
-                                   acc);
-                }
-            }
-        }
-        float* o = din + ((size_t)b * L.ci + ci) * n + i;
-        *o = accumulate ? *o + acc : acc;
-    }
-}
-
-// Partial weight gradients: part[slice][co][ci][k] = sum over one slice of the
-// (b, o) range of dz[b][co][o] in_eff[b][ci][o s + k - 1]; one thread per
-// (co, ci) pair of an 8 x 8 tile.  The slices are summed in a fixed order by
-// sum_slices_kernel, so the gradient does not depend on scheduling.
-__global__ void __launch_bounds__(64) conv_bwd_weight_kernel(const float* __restrict__ in, const float* __restrict__ dz,
-                                                             float* part, Layer L, int B, int slices) {
-    const int co = blockIdx.y * 8 + (threadIdx.x >> 3);
-    const int ci = blockIdx.z * 8 + (threadIdx.x & 7);
-    const size_t P = (size_t)L.hout * L.hout;
-    const size_t total = P * B;
-    const size_t per = (total + slices - 1) / slices;
-    const size_t p0 = (size_t)blockIdx.x * per, p1 = min(total, p0 + per);
-    if (co >= L.co || ci >= L.ci) return;
-    float acc[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-    for (size_t q = p0; q < p1; ++q) {
-        const int b = (int)(q / P);
-        const size_t o = q % P;
-        const int oy = (int)(o / L.hout), ox = (int)(o % L.hout);
-        const float g = __ldg(dz + ((size_t)b * L.co + co) * P + o);
-        if (g == 0.0f) continue;
-        const float* inc = in + ((size_t)b * L.ci + ci) * L.hin * L.hin;
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-            acc[k] = fmaf(g, in_eff(inc, L.hin, L.up, oy * L.stride + k / 3 - 1, ox * L.stride + k % 3 - 1), acc[k]);
-    }
-    float* out = part + ((size_t)blockIdx.x * L.co * L.ci + (size_t)co * L.ci + ci) * 9;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) out[k] = acc[k];
 }
 
 // dW[i] = sum_s part[s][i], s in increasing order.
@@ -229,23 +135,16 @@ __global__ void mse_kernel(const float* __restrict__ v, const float* __restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-__global__ void adam_kernel(float* p, const float* __restrict__ g, float* m, float* s, __nv_bfloat16* wb, size_t n,
-                            float lr, float c1, float c2) {
+__global__ void adam_kernel(float* p, const float* __restrict__ g, float* m, float* s, size_t n, float lr, float c1,
+                            float c2) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = 0.9f * m[i] + 0.1f * gi;
         const float si = 0.999f * s[i] + 0.001f * gi * gi;
         m[i] = mi;
         s[i] = si;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(si / c2) + 1e-8f);
-        p[i] = pi;
-        wb[i] = __float2bfloat16_rn(pi);
+        p[i] = p[i] - lr * (mi / c1) / (sqrtf(si / c2) + 1e-8f);
     }
-}
-
-__global__ void to_bf16_kernel(const float* __restrict__ p, __nv_bfloat16* wb, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        wb[i] = __float2bfloat16_rn(p[i]);
 }
 
 inline int blocks_for(size_t n) {
@@ -262,10 +161,14 @@ struct lgnk_ws {
     std::vector<Layer> L;
     size_t nparams;
     float *p, *g, *am, *as;     // master weights, gradients, Adam moments
-    __nv_bfloat16* wb;          // bf16 weights
     float *x, *e0, *e1, *e2, *e3, *r4, *d2, *r5, *d1, *z6;   // activations
     float *ga, *gb, *gc;        // gradient scratch (largest activation each)
     float* wpart;               // per-slice weight-gradient partials
+    __nv_bfloat16* planes;      // bf16 planes of a GEMM operand (umma::split_planes_kernel)
+    size_t planes_cap;          // elements of one plane it holds
+    float* gpart;               // split-K partial tiles of the FWD and BWD_DATA GEMMs
+    size_t gpart_cap;           // floats it holds
+    int* derr;                  // set by a tensor-core kernel whose wait ran out
     double* partial;
     double* hres;
     long long steps;
@@ -295,23 +198,119 @@ lgnk_status ws_alloc_n(lgnk_ws* w, size_t n, T** out) {
 
 size_t act_size(const lgnk_ws* w, int layer_out_c, int side, int B) { return (size_t)B * layer_out_c * side * side; }
 
-cudaError_t conv_fwd(lgnk_ws* w, int l, const float* in, float* out, float* r, const float* add, int relu, float scale,
-                     int B) {
-    const Layer& L = w->L[l];
-    const int tiles = (L.hout + 15) / 16;
-    dim3 grid(tiles * tiles, (L.co + kCo - 1) / kCo, B);
-    conv_fwd_kernel<<<grid, kT, 0, w->stream>>>(in, w->wb + L.woff, w->p + L.boff, out, r, add, L, relu, scale);
+// planes of src [B][C][h][h] into w->planes (channels padded to cp)
+cudaError_t split_planes(lgnk_ws* w, const float* src, int B, int C, int h, int cp, size_t* plane_elems) {
+    *plane_elems = (size_t)B * h * h * cp;
+    if (*plane_elems > w->planes_cap) return cudaErrorInvalidValue;
+    const size_t n = (size_t)B * h * h * (cp / 8);
+    umma::split_planes_kernel<<<blocks_for(n), kT, 0, w->stream>>>(src, w->planes, B, C, h, cp);
     return cudaGetLastError();
 }
 
+// CTAs a GEMM launch should reach: two per SM
+constexpr int kGemmCtas = 2 * 152;
+
+// K slices of a FWD / BWD_DATA GEMM with `tiles` output tiles and `chunks` K
+// chunks: enough slices to give about two CTAs per SM, each at least two
+// chunks (1 when the tiles alone fill the GPU)
+inline int split_slices(int tiles, int chunks) {
+    if (tiles >= kGemmCtas) return 1;
+    const int s = std::min((kGemmCtas + tiles - 1) / tiles, std::max(1, chunks / 2));
+    const int cps = (chunks + s - 1) / s;
+    return (chunks + cps - 1) / cps;
+}
+
+cudaError_t launch_gemm(lgnk_ws* w, umma::ConvGemm& g, int grid_x, int grid_y, int grid_z) {
+    g.stages = LGNK_CONV_STAGES;
+    const size_t smem = (size_t)g.stages * umma::stage_bytes(g.kind, g.bn);
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, umma::conv_gemm_kernel);
+    if (e == cudaSuccess && smem + fa.sharedSizeBytes > (size_t)optin) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(umma::conv_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    g.err = w->derr;
+    umma::conv_gemm_kernel<<<dim3(grid_x, grid_y, grid_z), umma::kThreads, smem, w->stream>>>(g);
+    return cudaGetLastError();
+}
+
+// a FWD or BWD_DATA GEMM, split along K when its tiles do not fill the GPU
+cudaError_t launch_gemm_split(lgnk_ws* w, umma::ConvGemm& g, int grid_y) {
+    const int gx = (g.M + umma::BM - 1) / umma::BM;
+    const int chunks = (g.K + umma::BK - 1) / umma::BK;
+    const int splits = split_slices(gx * grid_y, chunks);
+    g.chunks_per_split = (chunks + splits - 1) / splits;
+    g.part = w->gpart;
+    if (splits > 1 && (size_t)splits * g.M * g.N > w->gpart_cap) return cudaErrorInvalidValue;
+    cudaError_t e = launch_gemm(w, g, gx, grid_y, splits);
+    if (e != cudaSuccess || splits == 1) return e;
+    umma::finish_split_kernel<<<blocks_for((size_t)g.M * g.N), kT, 0, w->stream>>>(g, splits);
+    return cudaGetLastError();
+}
+
+umma::ConvGemm gemm_base(const Layer& L, int kind, int B) {
+    umma::ConvGemm g{};
+    g.kind = kind;
+    g.ci = L.ci;
+    g.co = L.co;
+    g.stride = L.stride;
+    g.up = L.up;
+    g.hin = L.hin;
+    g.hout = L.hout;
+    g.batch = B;
+    return g;
+}
+
+// out = scale (act(conv(in) + b) + add), r = act(conv(in) + b) (tensor-core GEMM)
+cudaError_t conv_fwd(lgnk_ws* w, int l, const float* in, float* out, float* r, const float* add, int relu, float scale,
+                     int B) {
+    const Layer& L = w->L[l];
+    umma::ConvGemm g = gemm_base(L, umma::FWD, B);
+    g.M = B * L.hout * L.hout;
+    g.N = L.co;
+    g.K = 9 * L.cpi;
+    g.cp = L.cpi;
+    g.bn = L.bnf;
+    cudaError_t e = split_planes(w, in, B, L.ci, L.hin, L.cpi, &g.plane_elems);
+    if (e != cudaSuccess) return e;
+    g.planes = w->planes;
+    g.w = L.wf;
+    g.wld = L.ldf;
+    g.out = out;
+    g.r = r;
+    g.add = add;
+    g.bias = w->p + L.boff;
+    g.relu = relu;
+    g.scale = scale;
+    return launch_gemm_split(w, g, L.rowsf / L.bnf);
+}
+
+// weight and bias gradients of layer l from its input `in` and output gradient
+// dz; with din, also the input gradient (added to din when accumulate)
 cudaError_t conv_bwd(lgnk_ws* w, int l, const float* in, const float* dz, float* din, int accumulate, int B) {
     const Layer& L = w->L[l];
-    // weight and bias gradients
-    const size_t P = (size_t)L.hout * L.hout * B;
-    const int slices = (int)std::min<size_t>(kMaxSlices, (P + 1023) / 1024);
-    dim3 gw(slices, (L.co + 7) / 8, (L.ci + 7) / 8);
-    conv_bwd_weight_kernel<<<gw, 64, 0, w->stream>>>(in, dz, w->wpart, L, B, slices);
-    cudaError_t e = cudaGetLastError();
+    // weight gradient: D[co][(ci, tap)] over the batch's pixels, K split into slices
+    umma::ConvGemm g = gemm_base(L, umma::BWD_WEIGHT, B);
+    g.M = L.co;
+    g.N = L.ci * 9;
+    g.K = B * L.hout * L.hout;
+    g.bn = std::min(128, round_up(g.N, 16));
+    const int gx = (g.M + umma::BM - 1) / umma::BM, gy = (g.N + g.bn - 1) / g.bn;
+    const int chunks = (g.K + umma::BK - 1) / umma::BK;
+    int slices = std::min(kMaxSlices, std::min(chunks, std::max(1, (2 * 152 + gx * gy - 1) / (gx * gy))));
+    g.chunks_per_split = (chunks + slices - 1) / slices;
+    slices = (chunks + g.chunks_per_split - 1) / g.chunks_per_split;
+    g.a = dz;
+    g.x = in;
+    g.out = w->wpart;
+    cudaError_t e = launch_gemm(w, g, gx, gy, slices);
     if (e != cudaSuccess) return e;
     const size_t nw = (size_t)L.co * L.ci * 9;
     sum_slices_kernel<<<blocks_for(nw), kT, 0, w->stream>>>(w->wpart, w->g + L.woff, nw, slices);
@@ -320,10 +319,32 @@ cudaError_t conv_bwd(lgnk_ws* w, int l, const float* in, const float* dz, float*
     bias_grad_kernel<<<L.co, kT, 0, w->stream>>>(dz, w->g + L.boff, L.co, (size_t)L.hout * L.hout, B);
     e = cudaGetLastError();
     if (e != cudaSuccess || din == nullptr) return e;
-    const size_t n = (size_t)L.hin * L.hin;
-    dim3 gd((int)std::min<size_t>((n + kT - 1) / kT, 1024), L.ci, B);
-    conv_bwd_data_kernel<<<gd, kT, 0, w->stream>>>(dz, w->wb + L.woff, din, L, accumulate);
-    return cudaGetLastError();
+    // data gradient: D[input pixel][ci]
+    umma::ConvGemm d = gemm_base(L, umma::BWD_DATA, B);
+    d.M = B * L.hin * L.hin;
+    d.N = L.ci;
+    d.K = 9 * (L.up ? 4 : 1) * L.cpo;
+    d.cp = L.cpo;
+    d.bn = L.bnd;
+    e = split_planes(w, dz, B, L.co, L.hout, L.cpo, &d.plane_elems);
+    if (e != cudaSuccess) return e;
+    d.planes = w->planes;
+    d.w = L.wd;
+    d.wld = L.ldd;
+    d.out = din;
+    d.accumulate = accumulate;
+    return launch_gemm_split(w, d, L.rowsd / L.bnd);
+}
+
+// refresh the GEMMs' bf16 weight matrices from the master weights
+cudaError_t pack_weights(lgnk_ws* w) {
+    for (const Layer& L : w->L) {
+        const size_t n = (size_t)L.rowsf * L.ldf + (size_t)L.rowsd * L.ldd;
+        pack_wmats_kernel<<<blocks_for(n), kT, 0, w->stream>>>(w->p, L);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 lgnk_status forward_pass(lgnk_ws* w, int B, const float* T, const float* R, float* v) {
@@ -405,8 +426,43 @@ lgnk_status lgnk_ws_create(int image_m, int base_channels, int max_batch, float 
         return st;
     };
     if ((s = ws_alloc_n(w, off, &w->p)) || (s = ws_alloc_n(w, off, &w->g)) || (s = ws_alloc_n(w, off, &w->am)) ||
-        (s = ws_alloc_n(w, off, &w->as)) || (s = ws_alloc_n(w, off, &w->wb)))
+        (s = ws_alloc_n(w, off, &w->as)) || (s = ws_alloc_n(w, 1, &w->derr)))
         return fail(s);
+    // the GEMMs' bf16 weight matrices (N per CTA up to 256, rows and K padded)
+    size_t pmax = 0;
+    for (Layer& L : w->L) {
+        const int R = L.up ? 4 : 1;
+        L.cpi = round_up(L.ci, 8);
+        L.cpo = round_up(L.co, 8);
+        L.bnf = std::min(256, round_up(L.co, 16));
+        L.rowsf = round_up(L.co, L.bnf);
+        L.ldf = round_up(9 * L.cpi, umma::BK);
+        L.bnd = std::min(256, round_up(L.ci, 16));
+        L.rowsd = round_up(L.ci, L.bnd);
+        L.ldd = round_up(9 * R * L.cpo, umma::BK);
+        pmax = std::max(pmax, (size_t)B * L.hin * L.hin * L.cpi);
+        pmax = std::max(pmax, (size_t)B * L.hout * L.hout * L.cpo);
+        if ((s = ws_alloc_n(w, (size_t)L.rowsf * L.ldf, &L.wf)) || (s = ws_alloc_n(w, (size_t)L.rowsd * L.ldd, &L.wd)))
+            return fail(s);
+    }
+    w->planes_cap = pmax;
+    if ((s = ws_alloc_n(w, 3 * pmax, &w->planes))) return fail(s);
+    // split-K partials: the largest splits x M x N any batch size up to max_batch needs
+    size_t gmax = 1;
+    for (int b = 1; b <= B; ++b) {
+        for (const Layer& L : w->L) {
+            const int R = L.up ? 4 : 1;
+            const long long Mf = (long long)b * L.hout * L.hout, Md = (long long)b * L.hin * L.hin;
+            const int tf = (int)((Mf + umma::BM - 1) / umma::BM) * (L.rowsf / L.bnf);
+            const int td = (int)((Md + umma::BM - 1) / umma::BM) * (L.rowsd / L.bnd);
+            const int sf = split_slices(tf, (9 * L.cpi + umma::BK - 1) / umma::BK);
+            const int sd = split_slices(td, (9 * R * L.cpo + umma::BK - 1) / umma::BK);
+            if (sf > 1) gmax = std::max(gmax, (size_t)sf * (size_t)Mf * L.co);
+            if (sd > 1) gmax = std::max(gmax, (size_t)sd * (size_t)Md * L.ci);
+        }
+    }
+    w->gpart_cap = gmax;
+    if ((s = ws_alloc_n(w, gmax, &w->gpart))) return fail(s);
     const size_t big = act_size(w, c, m, B);   // the largest activation: e0
     if ((s = ws_alloc_n(w, act_size(w, 2, m, B), &w->x)) || (s = ws_alloc_n(w, big, &w->e0)) ||
         (s = ws_alloc_n(w, act_size(w, 2 * c, m / 2, B), &w->e1)) ||
@@ -431,7 +487,7 @@ lgnk_status lgnk_ws_create(int image_m, int base_channels, int max_batch, float 
     if (cudaMemsetAsync(w->p, 0, off * sizeof(float), w->stream) != cudaSuccess ||
         cudaMemsetAsync(w->am, 0, off * sizeof(float), w->stream) != cudaSuccess ||
         cudaMemsetAsync(w->as, 0, off * sizeof(float), w->stream) != cudaSuccess ||
-        cudaMemsetAsync(w->wb, 0, off * sizeof(__nv_bfloat16), w->stream) != cudaSuccess)
+        cudaMemsetAsync(w->derr, 0, sizeof(int), w->stream) != cudaSuccess || pack_weights(w) != cudaSuccess)
         return fail(LGNK_ERR_CUDA);
     *out = w;
     return LGNK_OK;
@@ -444,8 +500,7 @@ const char* lgnk_ws_last_error(const lgnk_ws* w) { return w ? w->err : "null net
 lgnk_status lgnk_ws_set_params(lgnk_ws* w, const float* params) {
     if (w == nullptr || params == nullptr) return LGNK_ERR_INVALID_ARG;
     WS_CHECK(cudaMemcpyAsync(w->p, params, w->nparams * sizeof(float), cudaMemcpyDeviceToDevice, w->stream));
-    to_bf16_kernel<<<blocks_for(w->nparams), kT, 0, w->stream>>>(w->p, w->wb, w->nparams);
-    WS_CHECK(cudaGetLastError());
+    WS_CHECK(pack_weights(w));
     WS_CHECK(cudaMemsetAsync(w->am, 0, w->nparams * sizeof(float), w->stream));
     WS_CHECK(cudaMemsetAsync(w->as, 0, w->nparams * sizeof(float), w->stream));
     w->steps = 0;
@@ -527,13 +582,21 @@ lgnk_status lgnk_ws_train_step(lgnk_ws* w, int batch, const float* T, const floa
     // Adam
     w->steps++;
     const float c1 = 1.0f - powf(0.9f, (float)w->steps), c2 = 1.0f - powf(0.999f, (float)w->steps);
-    adam_kernel<<<blocks_for(w->nparams), kT, 0, w->stream>>>(w->p, w->g, w->am, w->as, w->wb, w->nparams, lr, c1, c2);
+    adam_kernel<<<blocks_for(w->nparams), kT, 0, w->stream>>>(w->p, w->g, w->am, w->as, w->nparams, lr, c1, c2);
     WS_CHECK(cudaGetLastError());
+    WS_CHECK(pack_weights(w));
     if (loss != nullptr) {
         launch_reduce(w->partial, nb, w->partial + 2048, w->stream);
         WS_CHECK(cudaGetLastError());
         WS_CHECK(cudaMemcpyAsync(w->hres, w->partial + 2048, sizeof(double), cudaMemcpyDeviceToHost, w->stream));
+        WS_CHECK(cudaMemcpyAsync(w->hres + 1, w->derr, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
         WS_CHECK(cudaStreamSynchronize(w->stream));
+        int bad = 0;
+        memcpy(&bad, w->hres + 1, sizeof(int));
+        if (bad != 0) {
+            snprintf(w->err, sizeof(w->err), "a tensor-core convolution gave up waiting for its MMAs");
+            return LGNK_ERR_INTERNAL;
+        }
         *loss = 0.5 * w->hres[0] / (double)nv / ((double)w->scale * w->scale);
     }
     return LGNK_OK;
