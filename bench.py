@@ -69,6 +69,14 @@ def job_throughput(step_ms: float, world: int) -> float:
     return world * 1000.0 / step_ms
 
 
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -618,9 +626,10 @@ def run_gpu(args):
     warm = None
     if args.warm_start:
         # learned warm start: 2048 solver-generated 128^2 training pairs, 256
-        # held-out pairs (about three minutes, so only on request)
+        # held-out pairs (under a minute with the tensor-core convolutions)
         from paper_1703_04446_gb300 import warmstart
         warm = warmstart.run()
+        warm["conv_peak_tflops"] = {"bf16": _bf16_peak(), "kind": "measured cuBLAS bf16 (burst)"}
     tts = None
     if not args.no_solve:
         torch.cuda.synchronize(dev)
@@ -709,6 +718,23 @@ def profile_case(args):
     `launches` times."""
     import torch
     from paper_1703_04446_gb300 import lgnk, synth
+    if args.profile_case == "ws":
+        # the warm-start network (c = 32) on a batch of 32 pairs of S^2 images: `launches`
+        # predictions (each 7 convolution GEMMs), then `launches` training steps
+        S, c, B = args.size, 32, 32
+        net = lgnk.WarmStart(S, c, B, 0.05)
+        net.set_params(torch.from_numpy(synth.warmstart_init(c, 0)))
+        rng = np.random.default_rng(0)
+        T, R = (torch.from_numpy(rng.uniform(size=(B, S, S)).astype(np.float32)).cuda() for _ in range(2))
+        vt = torch.from_numpy((0.05 * rng.normal(size=(B, 2, S // 2, S // 2))).astype(np.float32)).cuda()
+        for _ in range(args.launches):
+            v = net.predict(T, R)
+        for _ in range(args.launches):
+            net.train_step(T, R, vt, 1e-4, return_loss=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "ws", "size": S, "launches": args.launches,
+                          "checksum": float(v.double().abs().sum())}))
+        return
     S = args.size
     lo, hi = (0.0,) * 3, (1.0,) * 3
     ig = synth.GridSpec((S,) * 3, lo, hi)
@@ -763,12 +789,12 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true")
-    ap.add_argument("--profile-case", choices=["hess", "ell", "solve", "cont"], default=None,
+    ap.add_argument("--profile-case", choices=["hess", "ell", "solve", "cont", "ws"], default=None,
                     help="run only a short fixed invocation of one kernel (for ncu captures)")
     ap.add_argument("--size", type=int, default=128, help="image cells per axis of --profile-case")
     ap.add_argument("--launches", type=int, default=3, help="kernel launches of --profile-case")
-    ap.add_argument("--warm-start", action="store_true",
-                    help="also train and evaluate the learned warm start (2D 128^2 pairs, about 3 min)")
+    ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
+                    help="skip training and evaluating the learned warm start (2D 128^2 pairs, under a minute)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args)

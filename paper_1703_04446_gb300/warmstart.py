@@ -150,6 +150,32 @@ def stat_ratio(rows):
     return {"median": float(np.median(a)), "max": float(a.max())}
 
 
+def forward_flops(m: int, c: int) -> float:
+    """Multiply-adds x 2 of one forward pass on an m x m pair (the convolutions'
+    logical work, without the padding the tensor-core tiles add)."""
+    shapes = [(2, c, 1, 0, m), (c, 2 * c, 2, 0, m), (2 * c, 4 * c, 2, 0, m // 2), (4 * c, 8 * c, 2, 0, m // 4),
+              (8 * c, 4 * c, 1, 1, m // 8), (4 * c, 2 * c, 1, 1, m // 4), (2 * c, 2, 1, 0, m // 2)]
+    total = 0.0
+    for ci, co, s, up, hin in shapes:
+        ho = 2 * hin if up else hin // s
+        total += 2.0 * ho * ho * co * ci * 9
+    return total
+
+
+def time_prediction(net: lgnk.WarmStart, T, R, reps: int = 50):
+    """CUDA-event time of one prediction of one pair (ms)."""
+    out = torch.empty((1, 2, T.shape[-1] // 2, T.shape[-1] // 2), device=T.device)
+    for _ in range(3):
+        net.predict(T[:1], R[:1], out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        net.predict(T[:1], R[:1], out=out)
+    e1.record()
+    _sync()
+    return e0.elapsed_time(e1) / reps
+
+
 def run(n_train=2048, n_test=256, channels=32, epochs=30, batch=32, lr=1e-3, seed=0, log=None, alpha=None):
     over = {} if alpha is None else {"alpha": alpha}
     ctx = lgnk.Context(problem(**over))
@@ -172,6 +198,13 @@ def run(n_train=2048, n_test=256, channels=32, epochs=30, batch=32, lr=1e-3, see
     _sync()
     out["train_s"] = time.perf_counter() - t
     out["train_steps"] = len(losses)
+    fl = forward_flops(T.shape[-1], channels)
+    step_ms = 1e3 * out["train_s"] / max(len(losses), 1)
+    out["train_step_ms"] = step_ms
+    out["train_conv_tflops"] = 3.0 * fl * batch / (step_ms * 1e-3) / 1e12     # forward + two gradients
+    pm = time_prediction(net, Tt, Rt)
+    out["predict_ms"] = pm
+    out["predict_conv_tflops"] = fl / (pm * 1e-3) / 1e12
     out["loss_first"], out["loss_last"] = losses[0], float(np.mean(losses[-20:]))
     rows = evaluate(ctx, net, Tt, Rt)
     out["eval"] = summarize(rows)
