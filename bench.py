@@ -175,12 +175,19 @@ def algorithmic_bytes_hess(wl):
 
 
 # FP32 FLOPs (FMA = 2) of one voxel-step of the fused matvec in 3D for a
-# stationary velocity, counted from the separable trilinear evaluation: tangent
-# step 4 x (gradient planes, z-combination, J q, dv value, locate) plus state
-# updates = 849; adjoint step 4 x (dot-gradient stage, locate, scatter weights
-# and products) plus bookkeeping = 574 (stage positions are recorded by the
-# tangent sweep, not recomputed).
-HESS_FLOPS_PER_VOXEL_STEP = 1423
+# stationary velocity, counted from the kernel's formulation (the cell's
+# multilinear interpolant held as polynomial coefficients):
+#   tangent step: 4 stages x (locate 3 FFMA + 3 FADD, q / h 3 FMUL, per
+#     component value and gradient 11 FFMA, J q 1 FMUL + 2 FFMA, dv value
+#     7 FFMA) = 4 x 135, plus the RK4 state updates 18 FADD + 36 FFMA = 90 -> 630;
+#   adjoint step: 4 stages x (locate 3 FFMA + 3 FADD, coefficients of v . mu
+#     7 FMUL + 14 FFMA, its gradient 8 FFMA, nu 3 FMUL, scatter weights 3 FADD
+#     + 12 FMUL, corner block 24 FFMA) = 4 x 126, plus bookkeeping 12 FMUL +
+#     9 FFMA + 12 FADD = 42 -> 546.
+# The coefficients themselves (13 FADD per component when a stage enters a
+# new cell) depend on the data and are not counted; ncu's executed counts are
+# in the committed profile.
+HESS_FLOPS_PER_VOXEL_STEP = 1176
 
 
 def algorithmic_flops_hess(wl):
@@ -208,9 +215,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    or None when the kernel source has changed since that capture."""
+def profiled_counters():
+    """Counters of the fused kernel from the committed ncu summary (DRAM bytes
+    and warp instructions per launch), or {} when the kernel source has changed
+    since that capture."""
     path = os.path.join(ROOT, "profiles", "hess_transport_128.txt")
     vals = {}
     try:
@@ -219,13 +227,16 @@ def profiled_traffic():
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     except OSError:
-        return None
+        return {}
     if vals.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    try:
-        return int(float(vals["traffic_bytes_per_launch"]))
-    except (KeyError, ValueError):
-        return None
+        return {}
+    out = {}
+    for key, name in (("traffic", "traffic_bytes_per_launch"), ("warp_inst", "smsp__inst_executed.sum")):
+        try:
+            out[key] = int(float(vals[name].split()[0]))
+        except (KeyError, ValueError, IndexError):
+            pass
+    return out
 
 
 def assembled_matvec(ctx, v, T, dv, stream, reps=50):
@@ -659,12 +670,13 @@ def run_gpu(args):
         _, reps = lgnk.lgnk_solve_multilevel(prob, tT, tR, 3, max_gn=2 * args.max_gn, gn_grad_rtol=1e-3, max_pcg=50,
                                              pcg_rtol=0.1, gn_grad_atol=1e-3 * g_zero)
         torch.cuda.synchronize(dev)
-        tts["other_workloads"] = other_solves(dev, args.max_gn)
         tts["multilevel_3"] = {"seconds": time.perf_counter() - t0,
+                               "level_seconds": [r["seconds"] for r in reps],
                                "gn_iters": [r["gn_iters"] for r in reps], "pcg_iters": [r["pcg_iters"] for r in reps],
                                "finest_grad_ratio": reps[-1]["g"] / reps[-1]["g0"],
                                "grad_over_zero_start_grad": reps[-1]["g"] / g_zero, "J": reps[-1]["J"],
                                "status": reps[-1]["status_name"]}
+        tts["other_workloads"] = other_solves(dev, args.max_gn)
 
     if rank != 0:
         return
@@ -675,7 +687,8 @@ def run_gpu(args):
     achieved = flops / (kern_avg_ms * 1e-3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak, peak_mhz = fp32_peak_tflops(sms)
-    traffic = profiled_traffic()
+    prof = profiled_counters()
+    traffic = prof.get("traffic")
     n = int(tv.numel())
     M = int(tT.numel())
     line = {
@@ -695,7 +708,14 @@ def run_gpu(args):
                                   f"{peak_mhz:.0f} MHz", "sms": sms,
                      "hbm": {"algorithmic_bytes": alg, "achieved_gbs": alg / (kern_avg_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak, "frac": alg / (kern_avg_ms * 1e-3) / 1e9 / hbm_peak,
-                             "peak_kind": peak_kind}},
+                             "peak_kind": peak_kind},
+                     # the kernel is bound by instruction issue: warp instructions (one ncu capture)
+                     # per launch over its live time, against 4 issue slots per SM and clock
+                     "issue": None if "warp_inst" not in prof else {
+                         "warp_inst_per_launch": prof["warp_inst"],
+                         "achieved_ginst_s": prof["warp_inst"] / (kern_avg_ms * 1e-3) / 1e9,
+                         "peak_ginst_s": sms * 4 * peak_mhz * 1e6 / 1e9,
+                         "frac": prof["warp_inst"] / (kern_avg_ms * 1e-3) / (sms * 4 * peak_mhz * 1e6)}},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "extra": {"forward_voxel_steps_per_s": voxel_steps / (fwd_ms * 1e-3), "forward_ms": fwd_ms,

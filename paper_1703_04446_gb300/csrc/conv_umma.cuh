@@ -148,34 +148,47 @@ __device__ __forceinline__ float a_elem(const ConvGemm& g, int row, int k) {
     return __ldg(g.a + ((size_t)b * g.co + row) * P + o);
 }
 
-// The 16-byte chunks (three planes) of A row `row`, k = k0 .. k0 + 7, for FWD
-// and BWD_DATA: K runs over (tap[, up position], channel) with the channel
-// fastest, so a chunk is 8 channels of one source pixel, one 16-byte load per
-// plane from the NHWC planes (zero where the tap falls outside).
-__device__ __forceinline__ void a_chunk_planes(const ConvGemm& g, int row, int k0, uint4* v) {
+// The row of A a thread gathers for FWD and BWD_DATA, decomposed once: its
+// image and pixel coordinates (rows past M are marked invalid).
+struct RowCtx {
+    bool valid;
+    int b, y, x;     // FWD: output pixel (oy, ox); BWD_DATA: input pixel (iy, ix)
+};
+
+__device__ __forceinline__ RowCtx row_ctx(const ConvGemm& g, int row) {
+    RowCtx r;
+    r.valid = row < g.M;
+    const int h = g.kind == FWD ? g.hout : g.hin;
+    const int P = h * h;
+    r.b = row / P;
+    const int p = row - r.b * P;
+    r.y = p / h;
+    r.x = p - r.y * h;
+    return r;
+}
+
+// The 16-byte chunks (three planes) of A at the thread's row for the K
+// position `pos` (tap, or tap and up position) and channels c0 .. c0 + 7, for
+// FWD and BWD_DATA: K runs over (pos, channel) with the channel fastest, so a
+// chunk is 8 channels of one source pixel, one 16-byte load per plane from
+// the NHWC planes (zero where the tap falls outside).
+__device__ __forceinline__ void a_chunk_planes(const ConvGemm& g, const RowCtx& r, int pos, int c0, uint4* v) {
     v[0] = v[1] = v[2] = make_uint4(0u, 0u, 0u, 0u);
-    if (row >= g.M || k0 >= g.K) return;
-    const int pos = k0 / g.cp, c0 = k0 - pos * g.cp;
-    int b, y, x, h;
+    if (!r.valid || pos >= (g.up && g.kind == BWD_DATA ? 36 : 9)) return;
+    int y, x, h;
     if (g.kind == FWD) {
-        const int P = g.hout * g.hout;
-        b = row / P;
-        const int o = row - b * P, oy = o / g.hout, ox = o - oy * g.hout;
         const int ky = pos / 3, kx = pos - ky * 3;
-        int ey = oy * g.stride + ky - 1, ex = ox * g.stride + kx - 1;
+        const int ey = r.y * g.stride + ky - 1, ex = r.x * g.stride + kx - 1;
         const int he = g.up ? 2 * g.hin : g.hin;
         if (ey < 0 || ex < 0 || ey >= he || ex >= he) return;
         y = g.up ? ey >> 1 : ey;
         x = g.up ? ex >> 1 : ex;
         h = g.hin;
-    } else {   // BWD_DATA: rows are input pixels; pos = tap * R + up position
-        const int P = g.hin * g.hin;
-        b = row / P;
-        const int p = row - b * P, iy = p / g.hin, ix = p - iy * g.hin;
+    } else {   // BWD_DATA: pos = tap * R + up position
         const int R = g.up ? 4 : 1;
         const int t = pos / R, dd = pos - t * R;
         const int ky = t / 3, kx = t - ky * 3;
-        const int ey = g.up ? 2 * iy + (dd >> 1) : iy, ex = g.up ? 2 * ix + (dd & 1) : ix;
+        const int ey = g.up ? 2 * r.y + (dd >> 1) : r.y, ex = g.up ? 2 * r.x + (dd & 1) : r.x;
         const int ny = ey + 1 - ky, nx = ex + 1 - kx;
         if (ny < 0 || nx < 0) return;
         if (g.stride == 2 && ((ny | nx) & 1)) return;
@@ -184,7 +197,7 @@ __device__ __forceinline__ void a_chunk_planes(const ConvGemm& g, int row, int k
         if (y >= g.hout || x >= g.hout) return;
         h = g.hout;
     }
-    const size_t e = (((size_t)b * h + y) * h + x) * g.cp + c0;
+    const size_t e = (((size_t)r.b * h + y) * h + x) * g.cp + c0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) v[q] = __ldg(reinterpret_cast<const uint4*>(g.planes + q * g.plane_elems + e));
 }
@@ -280,6 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_gemm_kernel(const ConvGemm g
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = instr_desc(BM, g.bn);
 
+    const RowCtx rc = row_ctx(g, m0 + tid);    // FWD, BWD_DATA: this thread's A row
     bool failed = false;
     int issued = 0;
     int last = -1;      // index (from c_begin) of the last chunk whose MMAs were committed
@@ -287,8 +301,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_gemm_kernel(const ConvGemm g
         const int S = g.stages, i = c - c_begin, s = i % S;
         uint8_t* sa = smem + s * sbytes;
         uint8_t* sb = sa + 3 * kTileBytes;
-        if (i >= S) {   // the MMAs of chunk i - S read this stage (its use i / S - 1)
-            const bool ok = mbar_wait(&bar[s], (uint32_t)((i / S - 1) & 1));
+        if (i >= S) {   // the MMAs of chunk i - S read this stage (its use i / S - 1): one thread polls
+            const bool ok = tid != 0 || mbar_wait(&bar[s], (uint32_t)((i / S - 1) & 1));
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -302,13 +316,20 @@ __global__ void __launch_bounds__(kThreads, 1) conv_gemm_kernel(const ConvGemm g
                 gather_split<true>(g, m0 + row, k0 + kg * 8, sa, kTileBytes, chunk_off(row, kg));
             }
         } else {
+            // lanes along rows: neighbouring pixels; (pos, c0) of k0 + 8 kg stepped, not divided
+            int pos = k0 / g.cp, c0 = k0 - pos * g.cp;
 #pragma unroll 2
-            for (int kg = 0; kg < 8; ++kg) {                     // lanes along rows: neighbouring pixels
+            for (int kg = 0; kg < 8; ++kg) {
                 uint4 v[3];
-                a_chunk_planes(g, m0 + tid, k0 + kg * 8, v);
+                a_chunk_planes(g, rc, pos, c0, v);
                 const uint32_t off = chunk_off(tid, kg);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) *reinterpret_cast<uint4*>(sa + q * kTileBytes + off) = v[q];
+                c0 += 8;
+                if (c0 == g.cp) {
+                    c0 = 0;
+                    ++pos;
+                }
             }
         }
         // B: bn rows x 8 k groups
@@ -349,13 +370,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv_gemm_kernel(const ConvGemm g
     }
     if (!failed && last >= 0) {
         // the last commit covers every MMA issued before it
-        const bool ok = mbar_wait(&bar[last % g.stages], (uint32_t)((last / g.stages) & 1));
+        const bool ok = tid != 0 || mbar_wait(&bar[last % g.stages], (uint32_t)((last / g.stages) & 1));
         failed = __syncthreads_or(!ok);
     }
     if (failed) {
         if (tid == 0) atomicExch(g.err, 1);
         // once more, bounded, for whatever is still in flight
-        if (last >= 0) mbar_wait(&bar[last % g.stages], (uint32_t)((last / g.stages) & 1));
+        if (tid == 0 && last >= 0) mbar_wait(&bar[last % g.stages], (uint32_t)((last / g.stages) & 1));
     } else if (last >= 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int row = m0 + warp * 32 + lane;     // this thread's accumulator row (TMEM lane)
