@@ -167,20 +167,20 @@ __device__ __forceinline__ RowCtx row_ctx(const ConvGemm& g, int row) {
     return r;
 }
 
-// The 16-byte chunks (three planes) of A at the thread's row for the K
-// position `pos` (tap, or tap and up position) and channels c0 .. c0 + 7, for
-// FWD and BWD_DATA: K runs over (pos, channel) with the channel fastest, so a
-// chunk is 8 channels of one source pixel, one 16-byte load per plane from
-// the NHWC planes (zero where the tap falls outside).
-__device__ __forceinline__ void a_chunk_planes(const ConvGemm& g, const RowCtx& r, int pos, int c0, uint4* v) {
-    v[0] = v[1] = v[2] = make_uint4(0u, 0u, 0u, 0u);
-    if (!r.valid || pos >= (g.up && g.kind == BWD_DATA ? 36 : 9)) return;
+// The source of the 16-byte chunks (three planes) of A at the thread's row
+// for the K position `pos` (tap, or tap and up position) and channels c0 ..
+// c0 + 7, for FWD and BWD_DATA: K runs over (pos, channel) with the channel
+// fastest, so a chunk is 8 channels of one source pixel of the NHWC planes.
+// Returns false where the tap falls outside (the chunk is zero); e receives
+// the element offset of the chunk in one plane.
+__device__ __forceinline__ bool a_chunk_src(const ConvGemm& g, const RowCtx& r, int pos, int c0, size_t* e) {
+    if (!r.valid || pos >= (g.up && g.kind == BWD_DATA ? 36 : 9)) return false;
     int y, x, h;
     if (g.kind == FWD) {
         const int ky = pos / 3, kx = pos - ky * 3;
         const int ey = r.y * g.stride + ky - 1, ex = r.x * g.stride + kx - 1;
         const int he = g.up ? 2 * g.hin : g.hin;
-        if (ey < 0 || ex < 0 || ey >= he || ex >= he) return;
+        if (ey < 0 || ex < 0 || ey >= he || ex >= he) return false;
         y = g.up ? ey >> 1 : ey;
         x = g.up ? ex >> 1 : ex;
         h = g.hin;
@@ -190,17 +190,24 @@ __device__ __forceinline__ void a_chunk_planes(const ConvGemm& g, const RowCtx& 
         const int ky = t / 3, kx = t - ky * 3;
         const int ey = g.up ? 2 * r.y + (dd >> 1) : r.y, ex = g.up ? 2 * r.x + (dd & 1) : r.x;
         const int ny = ey + 1 - ky, nx = ex + 1 - kx;
-        if (ny < 0 || nx < 0) return;
-        if (g.stride == 2 && ((ny | nx) & 1)) return;
+        if (ny < 0 || nx < 0) return false;
+        if (g.stride == 2 && ((ny | nx) & 1)) return false;
         y = ny / g.stride;
         x = nx / g.stride;
-        if (y >= g.hout || x >= g.hout) return;
+        if (y >= g.hout || x >= g.hout) return false;
         h = g.hout;
     }
-    const size_t e = (((size_t)r.b * h + y) * h + x) * g.cp + c0;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) v[q] = __ldg(reinterpret_cast<const uint4*>(g.planes + q * g.plane_elems + e));
+    *e = (((size_t)r.b * h + y) * h + x) * g.cp + c0;
+    return true;
 }
+
+// 16 bytes global -> shared without passing through registers; with
+// valid == false the 16 shared bytes are zero-filled and nothing is read.
+__device__ __forceinline__ void cp_async16(uint8_t* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Three bf16 planes of an FP32 tensor [B][C][h][h] (NCHW) in NHWC order with
 // the channels padded to cp (a multiple of 8) by zeros: plane q, element
@@ -316,15 +323,17 @@ __global__ void __launch_bounds__(kThreads, 1) conv_gemm_kernel(const ConvGemm g
                 gather_split<true>(g, m0 + row, k0 + kg * 8, sa, kTileBytes, chunk_off(row, kg));
             }
         } else {
-            // lanes along rows: neighbouring pixels; (pos, c0) of k0 + 8 kg stepped, not divided
+            // lanes along rows: neighbouring pixels; (pos, c0) of k0 + 8 kg stepped, not divided.
+            // The 24 copies of a thread are all in flight before the wait below.
             int pos = k0 / g.cp, c0 = k0 - pos * g.cp;
-#pragma unroll 2
+#pragma unroll
             for (int kg = 0; kg < 8; ++kg) {
-                uint4 v[3];
-                a_chunk_planes(g, rc, pos, c0, v);
+                size_t e = 0;
+                const bool ok = a_chunk_src(g, rc, pos, c0, &e);
                 const uint32_t off = chunk_off(tid, kg);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) *reinterpret_cast<uint4*>(sa + q * kTileBytes + off) = v[q];
+                for (int q = 0; q < 3; ++q)
+                    cp_async16(sa + q * kTileBytes + off, g.planes + q * g.plane_elems + (ok ? e : 0), ok);
                 c0 += 8;
                 if (c0 == g.cp) {
                     c0 = 0;
@@ -341,9 +350,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv_gemm_kernel(const ConvGemm g
         } else {
             for (int it = tid; it < g.bn * 8; it += kThreads) {
                 const int row = it >> 3, kg = it & 7;
-                const uint4 v = *reinterpret_cast<const uint4*>(g.w + (size_t)(n0 + row) * g.wld + k0 + kg * 8);
-                *reinterpret_cast<uint4*>(sb + chunk_off(row, kg)) = v;
+                cp_async16(sb + chunk_off(row, kg), g.w + (size_t)(n0 + row) * g.wld + k0 + kg * 8, true);
             }
+            cp_async_wait_all();
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
