@@ -502,8 +502,7 @@ __device__ __forceinline__ void scatter_add(const DevGrid& g, AsmRow<D>& S, size
 // nu = d_y I(v, y, t)^T mu = grad_y (v . mu) of the interpolant.
 template <int D, class SC>
 __device__ __forceinline__ void stage_adjoint(const DevGrid& g, const float* __restrict__ V, SC& S,
-                                              size_t s0, const int* p, const float* f, const float* mu, float* nu) {
-    const int base = linear<D>(g, p);
+                                              size_t s0, int base, const float* f, const float* mu, float* nu) {
     float s_0, dx, dy;
     plane_dot<D>(g, V, s0, base, 0, f, mu, s_0, dx, dy);
     if (D == 3) {
@@ -643,9 +642,8 @@ __device__ __forceinline__ void stage_tangent_cached(const DevGrid& g, const flo
 
 template <int D, class SC>
 __device__ __forceinline__ void stage_adjoint_cached(const DevGrid& g, const float* __restrict__ V, SC& S,
-                                                     CellCache<D, false>& C, size_t s0, const int* p, const float* f,
+                                                     CellCache<D, false>& C, size_t s0, int base, const float* f,
                                                      const float* mu, float* nu) {
-    const int base = linear<D>(g, p);
     cache_cell<D, false>(g, V, nullptr, s0, base, C);
     // coefficients of the scalar interpolant of v . mu (its constant is not needed)
     float sc[1 << D];
@@ -810,6 +808,23 @@ __device__ __noinline__ void pic_hat(const DevGrid& g, const int* I0, const floa
     }
 }
 
+// What the forward sweep records of a stage for the adjoint sweep: the
+// stage's cell on the velocity grid (linear padded index) and its fractional
+// offsets in it, as one 16-byte word (f0, f1, f2 or 0, base).  The adjoint
+// then needs no second lookup of the stage position.
+template <int D>
+__device__ __forceinline__ float4 stage_word(const DevGrid& g, const int* p, const float* f) {
+    return make_float4(f[0], f[1], D == 3 ? f[D - 1] : 0.0f, __int_as_float(linear<D>(g, p)));
+}
+
+template <int D>
+__device__ __forceinline__ int stage_from_word(const float4 w, float* f) {
+    f[0] = w.x;
+    f[1] = w.y;
+    if (D == 3) f[D - 1] = w.z;
+    return __float_as_int(w.w);
+}
+
 // Slices of the stages of step k: t_k (2k), t_k + dt/2 (2k + 1, stages 2 and
 // 3), t_k + dt (2k + 2); a stationary field has the single slice 0.
 template <bool NS>
@@ -823,11 +838,21 @@ __device__ __forceinline__ void step_slices(const TraceArgs& A, int k, size_t& s
     }
 }
 
+// What the forward and tangent sweeps record of each stage for an adjoint
+// sweep (RM): 0 nothing; 1 the stage positions (u, u2, u3, u4 into pos[0 ..
+// 4d)), from which the adjoint looks the cells up again; 2 each stage's cell
+// and offsets (one 16-byte word per stage into cells[0..3]), so the adjoint
+// needs no lookup.  Transport records cells (the 128^3 matvec 0.706 -> 0.630
+// ms); the mass-preserving kernels record positions, whose record is a
+// quarter smaller: their local-memory traffic is what reaches DRAM, and the
+// brain-scale J^T measured 8.43 ms with positions against 8.87 ms with cells.
+enum RecordMode { REC_NONE = 0, REC_POS = 1, REC_CELL = 2 };
+
 // One RK4 step of the characteristic (Alg. 1 without the derivative), on the
-// displacement u.
-template <int D, bool NS, bool REC, bool CACHE>
-__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u, int k, float* rec,
-                                         CellCache<D, false>& C) {
+// displacement u, recording its stages as RM says.
+template <int D, bool NS, int RM, bool CACHE>
+__device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, float* u, int k, float* pos,
+                                         float4* rec, CellCache<D, false>& C) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -835,38 +860,42 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
     const float dt = A.dt, hdt = 0.5f * A.dt;
     int p[D];
     float f[D], vs[D], us[D], acc[D];
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[a] = u[a];
+        for (int a = 0; a < D; ++a) pos[a] = u[a];
     }
     locate<D>(A.vg, sv, u, p, f);
+    if (RM == REC_CELL) rec[0] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s1, p, f, C, vs);
     else stage_value<D>(A.vg, V, s1, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = vs[a]; us[a] = fmaf(hdt, vs[a], u[a]); }
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[D + a] = us[a];
+        for (int a = 0; a < D; ++a) pos[D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
+    if (RM == REC_CELL) rec[1] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
     else stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(hdt, vs[a], u[a]); }
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[2 * D + a] = us[a];
+        for (int a = 0; a < D; ++a) pos[2 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
+    if (RM == REC_CELL) rec[2] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s2, p, f, C, vs);
     else stage_value<D>(A.vg, V, s2, p, f, vs);
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = fmaf(2.0f, vs[a], acc[a]); us[a] = fmaf(dt, vs[a], u[a]); }
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[3 * D + a] = us[a];
+        for (int a = 0; a < D; ++a) pos[3 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
+    if (RM == REC_CELL) rec[3] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_value_cached<D>(A.vg, V, s4, p, f, C, vs);
     else stage_value<D>(A.vg, V, s4, p, f, vs);
     const float s6 = dt / 6.0f;
@@ -876,9 +905,9 @@ __device__ __forceinline__ void rk4_step(const TraceArgs& A, const float* V, flo
 
 // One RK4 step with the derivative recursion of Alg. 1 applied to dv:
 // D_s = I(dv, y_s, t_s) + d_y I(v, y_s, t_s) (dy + c_s dt D_{s-1}).
-template <int D, bool NS, bool REC, bool CACHE>
+template <int D, bool NS, int RM, bool CACHE>
 __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float* V, const float* dV, float* u,
-                                                 float* dy, int k, float* rec, CellCache<D, true>& C) {
+                                                 float* dy, int k, float* pos, float4* rec, CellCache<D, true>& C) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -887,11 +916,12 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
     int p[D];
     float f[D], us[D], q[D], vs[D], Jq[D], dvs[D], sv_acc[D], sd_acc[D], Ds;
     // stage 1 at y, offset dy
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[a] = u[a];
+        for (int a = 0; a < D; ++a) pos[a] = u[a];
     }
     locate<D>(A.vg, sv, u, p, f);
+    if (RM == REC_CELL) rec[0] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s1, p, f, dy, C, vs, Jq, dvs);
     else stage_tangent<D>(A.vg, V, dV, s1, p, f, dy, vs, Jq, dvs);
 #pragma unroll
@@ -903,11 +933,12 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         q[a] = fmaf(hdt, Ds, dy[a]);
     }
     // stage 2
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[D + a] = us[a];
+        for (int a = 0; a < D; ++a) pos[D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
+    if (RM == REC_CELL) rec[1] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s2, p, f, q, C, vs, Jq, dvs);
     else stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
@@ -919,11 +950,12 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         q[a] = fmaf(hdt, Ds, dy[a]);
     }
     // stage 3
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[2 * D + a] = us[a];
+        for (int a = 0; a < D; ++a) pos[2 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
+    if (RM == REC_CELL) rec[2] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s2, p, f, q, C, vs, Jq, dvs);
     else stage_tangent<D>(A.vg, V, dV, s2, p, f, q, vs, Jq, dvs);
 #pragma unroll
@@ -935,11 +967,12 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
         q[a] = fmaf(dt, Ds, dy[a]);
     }
     // stage 4
-    if (REC) {
+    if (RM == REC_POS) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[3 * D + a] = us[a];
+        for (int a = 0; a < D; ++a) pos[3 * D + a] = us[a];
     }
     locate<D>(A.vg, sv, us, p, f);
+    if (RM == REC_CELL) rec[3] = stage_word<D>(A.vg, p, f);
     if constexpr (CACHE) stage_tangent_cached<D>(A.vg, V, dV, s4, p, f, q, C, vs, Jq, dvs);
     else stage_tangent<D>(A.vg, V, dV, s4, p, f, q, vs, Jq, dvs);
     const float s6 = dt / 6.0f;
@@ -950,13 +983,11 @@ __device__ __forceinline__ void rk4_tangent_step(const TraceArgs& A, const float
     }
 }
 
-// Transpose of one tangent step: given lam (adjoint of the step's end point),
-// scatter the step's contribution into the gradient and return the adjoint of
-// its start.  The stage positions u, u2, u3, u4 were recorded by the forward
-// sweep; each stage's J^T mu and scatter share one pass over its corners.
+// Transpose of one tangent step from recorded stage positions (RM = 1): the
+// same as rk4_adjoint_step below, with each stage's cell looked up again.
 template <int D, bool NS, class SC, bool CACHE>
-__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, SC& S, const float* rec,
-                                                 float* lam, int k, CellCache<D, false>& C) {
+__device__ __forceinline__ void rk4_adjoint_step_pos(const TraceArgs& A, const float* V, SC& S, const float* rec,
+                                                     float* lam, int k, CellCache<D, false>& C) {
     size_t s1, s2, s4;
     step_slices<NS>(A, k, s1, s2, s4);
     Start<D> sv;
@@ -966,30 +997,72 @@ __device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float
     float f[D], us[D];
     float mu[D], nu[D], acc[D];
     const float c16 = dt / 6.0f, c13 = dt / 3.0f;
-    // stage 4: D4 = I(dv, y4) + J4 (dy + dt D3)
+    // stage 4
 #pragma unroll
     for (int a = 0; a < D; ++a) { mu[a] = c16 * lam[a]; us[a] = rec[3 * D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s4, p, f, mu, nu);
-    else stage_adjoint<D, SC>(A.vg, V, S, s4, p, f, mu, nu);
-    // stage 3: D3 = I(dv, y3) + J3 (dy + dt/2 D2)
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s4, linear<D>(A.vg, p), f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s4, linear<D>(A.vg, p), f, mu, nu);
+    // stage 3
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); us[a] = rec[2 * D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, p, f, mu, nu);
-    else stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
-    // stage 2: D2 = I(dv, y2) + J2 (dy + dt/2 D1)
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, linear<D>(A.vg, p), f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s2, linear<D>(A.vg, p), f, mu, nu);
+    // stage 2
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); us[a] = rec[D + a]; }
     locate<D>(A.vg, sv, us, p, f);
-    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, p, f, mu, nu);
-    else stage_adjoint<D, SC>(A.vg, V, S, s2, p, f, mu, nu);
-    // stage 1: D1 = I(dv, y) + J1 dy
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, linear<D>(A.vg, p), f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s2, linear<D>(A.vg, p), f, mu, nu);
+    // stage 1
 #pragma unroll
     for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); us[a] = rec[a]; }
     locate<D>(A.vg, sv, us, p, f);
-    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s1, p, f, mu, nu);
-    else stage_adjoint<D, SC>(A.vg, V, S, s1, p, f, mu, nu);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s1, linear<D>(A.vg, p), f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s1, linear<D>(A.vg, p), f, mu, nu);
+#pragma unroll
+    for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
+}
+
+// Transpose of one tangent step: given lam (adjoint of the step's end point),
+// scatter the step's contribution into the gradient and return the adjoint of
+// its start.  The cells and offsets of the stages were recorded by the
+// forward sweep (rec[0..3]); each stage's J^T mu and scatter share one pass.
+template <int D, bool NS, class SC, bool CACHE>
+__device__ __forceinline__ void rk4_adjoint_step(const TraceArgs& A, const float* V, SC& S, const float4* rec,
+                                                 float* lam, int k, CellCache<D, false>& C) {
+    size_t s1, s2, s4;
+    step_slices<NS>(A, k, s1, s2, s4);
+    const float dt = A.dt, hdt = 0.5f * A.dt;
+    float f[D];
+    float mu[D], nu[D], acc[D];
+    const float c16 = dt / 6.0f, c13 = dt / 3.0f;
+    int base;
+    // stage 4: D4 = I(dv, y4) + J4 (dy + dt D3)
+#pragma unroll
+    for (int a = 0; a < D; ++a) mu[a] = c16 * lam[a];
+    base = stage_from_word<D>(rec[3], f);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s4, base, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s4, base, f, mu, nu);
+    // stage 3: D3 = I(dv, y3) + J3 (dy + dt/2 D2)
+#pragma unroll
+    for (int a = 0; a < D; ++a) { acc[a] = nu[a]; mu[a] = fmaf(c13, lam[a], dt * nu[a]); }
+    base = stage_from_word<D>(rec[2], f);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, base, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s2, base, f, mu, nu);
+    // stage 2: D2 = I(dv, y2) + J2 (dy + dt/2 D1)
+#pragma unroll
+    for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c13, lam[a], hdt * nu[a]); }
+    base = stage_from_word<D>(rec[1], f);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s2, base, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s2, base, f, mu, nu);
+    // stage 1: D1 = I(dv, y) + J1 dy
+#pragma unroll
+    for (int a = 0; a < D; ++a) { acc[a] += nu[a]; mu[a] = fmaf(c16, lam[a], hdt * nu[a]); }
+    base = stage_from_word<D>(rec[0], f);
+    if constexpr (CACHE) stage_adjoint_cached<D, SC>(A.vg, V, S, C, s1, base, f, mu, nu);
+    else stage_adjoint<D, SC>(A.vg, V, S, s1, base, f, mu, nu);
 #pragma unroll
     for (int a = 0; a < D; ++a) lam[a] += acc[a] + nu[a];
 }
@@ -1213,24 +1286,26 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
         tcache.key = -1;
         CellCache<D, false> vcache;   // v corners for the forward and adjoint sweeps
         vcache.key = -1;
-        // stage positions of every step, recorded for the adjoint sweep in a
-        // per-thread local array as 16-byte words (4D floats per step).  Kept
+        // the stages of every step, recorded for the adjoint sweep (RecordMode)
+        // in a per-thread local array as 16-byte words.  Kept
         // in shared memory instead, the full record (2 CTAs x 96 KB on the
         // 128^3 matvec) shrank the L1 that the gathers use and measured slower
         // (0.828 against 0.814 ms); keeping only each step's start there and
         // recomputing the other positions in the adjoint sweep measured 0.974
         // ms, and on the brain-scale mass-preserving J^T 9.56 against 8.47 ms.
-        float4 lrec[ADJOINT ? LGNK_MAX_STEPS * D : 1];
+        constexpr int RM = !ADJOINT ? REC_NONE : (MODEL == LGNK_TRANSPORT ? REC_CELL : REC_POS);
+        constexpr int WPS = RM == REC_CELL ? 4 : D;     // 16-byte words per step
+        float4 lrec[ADJOINT ? LGNK_MAX_STEPS * WPS : 1];
 
 #pragma unroll 1
         for (int k = 0; k < A.N; ++k) {
-            float rec[4 * D];
-            if (TANGENT) rk4_tangent_step<D, NS, ADJOINT, CACHE>(A, V, dV, u, dy, k, rec, tcache);
-            else rk4_step<D, NS, ADJOINT, CACHE>(A, V, u, k, rec, vcache);
-            if constexpr (ADJOINT) {
+            float4* rec = lrec + (ADJOINT ? WPS * k : 0);
+            float pos[4 * D];
+            if (TANGENT) rk4_tangent_step<D, NS, RM, CACHE>(A, V, dV, u, dy, k, pos, rec, tcache);
+            else rk4_step<D, NS, RM, CACHE>(A, V, u, k, pos, rec, vcache);
+            if constexpr (RM == REC_POS) {
 #pragma unroll
-                for (int w = 0; w < D; ++w)
-                    lrec[k * D + w] = make_float4(rec[4 * w], rec[4 * w + 1], rec[4 * w + 2], rec[4 * w + 3]);
+                for (int w = 0; w < D; ++w) rec[w] = make_float4(pos[4 * w], pos[4 * w + 1], pos[4 * w + 2], pos[4 * w + 3]);
             }
         }
         if (A.yout != nullptr) {
@@ -1316,16 +1391,20 @@ __global__ void __launch_bounds__(LGNK_BLOCK, (TraceOccupancy<D, MODEL, MODE>::v
         if (ADJOINT) {
 #pragma unroll 1
             for (int k = A.N - 1; k >= 0; --k) {
-                float rec[4 * D];
+                if constexpr (RM == REC_CELL) {
+                    rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, lrec + WPS * k, lam, k, vcache);
+                } else {
+                    float pos[4 * D];
 #pragma unroll
-                for (int w = 0; w < D; ++w) {
-                    const float4 word = lrec[k * D + w];
-                    rec[4 * w] = word.x;
-                    rec[4 * w + 1] = word.y;
-                    rec[4 * w + 2] = word.z;
-                    rec[4 * w + 3] = word.w;
+                    for (int w = 0; w < D; ++w) {
+                        const float4 word = lrec[WPS * k + w];
+                        pos[4 * w] = word.x;
+                        pos[4 * w + 1] = word.y;
+                        pos[4 * w + 2] = word.z;
+                        pos[4 * w + 3] = word.w;
+                    }
+                    rk4_adjoint_step_pos<D, NS, SC, CACHE>(A, V, S, pos, lam, k, vcache);
                 }
-                rk4_adjoint_step<D, NS, SC, CACHE>(A, V, S, rec, lam, k, vcache);
             }
             scatter_finish<D>(A.vg, S);
             if constexpr (MODE == MODE_ASM) {
