@@ -1137,15 +1137,21 @@ __device__ __forceinline__ void ell_scatter(const EllArgs& A, long long key, con
         red_vec(G + corner_elem<D>(A.vg, (size_t)key, 0, c & 1, (c >> 1) & 1, (c >> 2) & 1), b + c * D, w);
 }
 
-// Scatter of the first blocks of a warp's rows with neighbouring rows paired:
-// voxels next to each other in x mostly trace through the same velocity cell,
-// so a run of lanes with equal keys adds its weighted blocks two by two through
-// shuffles before the reductions, and only the lane at an even position of the
-// run reduces (about half the global reductions).  Every lane of the warp calls
-// it; lanes without a block pass a key no other lane has.
+// Scatter of the first blocks of a warp's rows with neighbouring rows merged:
+// voxels next to each other in x mostly trace through the same velocity cell
+// or the next one along x.  A run of lanes with equal keys adds its weighted
+// blocks two by two through shuffles and only the lane at an even position of
+// the run reduces (about half the global reductions); then a reducing lane
+// whose next reducing lane holds the cell one step along x (key + 1: corner
+// (1, cy, cz) of cell k is node k + 1 + cy mx + cz mx my, corner (0, cy, cz)
+// of cell k + 1) hands it the four corner vectors of that face and reduces
+// only its other four corners.  Every lane of the warp calls it; lanes
+// without a block pass a key no other lane has.
 template <int D>
-__device__ __forceinline__ void ell_scatter_paired(const EllArgs& A, long long key, const float* b, float w) {
-    constexpr int B = (1 << D) * D;
+__device__ __forceinline__ void ell_scatter_merged(const EllArgs& A, long long key, const float* b, float w) {
+    constexpr int C = 1 << D, B = C * D;
+    using VT = typename VecT<D>::type;
+    VT* G = static_cast<VT*>(A.G);
     const int lane = threadIdx.x & 31;
     const long long prev = __shfl_up_sync(0xffffffffu, key, 1);
     const long long next = __shfl_down_sync(0xffffffffu, key, 1);
@@ -1160,8 +1166,32 @@ __device__ __forceinline__ void ell_scatter_paired(const EllArgs& A, long long k
         const float o = __shfl_down_sync(0xffffffffu, wb[k], 1);
         if (absorber) wb[k] += o;
     }
-    if (!absorbed && key >= 0) ell_scatter<D>(A, key, wb, 1.0f);
+    const bool reducer = !absorbed && key >= 0;
+    const unsigned red = __ballot_sync(0xffffffffu, reducer);
+    const unsigned above = lane == 31 ? 0u : red & (0xfffffffeu << lane);
+    const unsigned below = red & ((1u << lane) - 1u);
+    const int nxt = above != 0u ? __ffs((int)above) - 1 : lane;     // the next and previous reducing lanes
+    const int prv = below != 0u ? 31 - __clz((int)below) : lane;
+    const long long knext = __shfl_sync(0xffffffffu, key, nxt);
+    const long long kprev = __shfl_sync(0xffffffffu, key, prv);
+    const bool give = reducer && nxt != lane && knext == key + 1;
+    const bool take = reducer && prv != lane && kprev + 1 == key;
+#pragma unroll
+    for (int c = 1; c < C; c += 2) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const float o = __shfl_sync(0xffffffffu, wb[c * D + q], prv);
+            if (take) wb[(c - 1) * D + q] += o;
+        }
+    }
+    if (reducer) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            if (!((c & 1) && give))
+                red_vec(G + corner_elem<D>(A.vg, (size_t)key, 0, c & 1, (c >> 1) & 1, (c >> 2) & 1), wb + c * D, 1.0f);
+    }
 }
+
 
 template <int D, int EMODE>
 __global__ void __launch_bounds__(kEllBlock) ell_kernel(const EllArgs A) {
@@ -1196,8 +1226,8 @@ __global__ void __launch_bounds__(kEllBlock) ell_kernel(const EllArgs A) {
     } else {
         s = valid ? A.r[i] : 0.0f;
     }
-    // the first block: paired across the warp; keys are non-negative element offsets
-    ell_scatter_paired<D>(A, n > 0 ? kr[0] : -1 - (long long)(threadIdx.x & 31), br[0], s);
+    // the first block: merged across the warp; keys are non-negative element offsets
+    ell_scatter_merged<D>(A, n > 0 ? kr[0] : -1 - (long long)(threadIdx.x & 31), br[0], s);
 #pragma unroll
     for (int j = 1; j < RB; ++j)
         if (j < n) ell_scatter<D>(A, kr[j], br[j], s);

@@ -11,6 +11,7 @@ CASES = {
     "2d_transport_64": ((64, 64), (32, 32), (0, 0), (1, 1), 1, 4, "transport", "diffusion", 4.0),
     "2d_transport_ragged_K3": ((37, 29), (19, 15), (-0.2, 0.0), (1.1, 1.3), 3, 5, "transport", "curvature", 3.0),
     "2d_continuity_K5": ((48, 48), (24, 24), (0, 0), (1, 1), 5, 16, "continuity", "elastic", 3.0),
+    "2d_transport_tiny": ((11, 9), (6, 5), (0, 0), (1.1, 0.9), 1, 3, "transport", "diffusion", 1.5),
     "3d_transport_ragged": ((20, 18, 17), (10, 9, 9), (0, 0, 0), (1, 1, 1), 1, 8, "transport", "diffusion", 2.5),
     "3d_transport_K2_N1": ((12, 12, 12), (6, 6, 6), (0, 0, 0), (1, 1, 1), 2, 1, "transport", "diffusion", 2.0),
     "3d_continuity_K2": ((16, 20, 12), (8, 10, 6), (0, 0, 0), (1.0, 1.25, 0.75), 2, 3, "continuity", "diffusion", 2.0),
