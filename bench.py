@@ -180,14 +180,16 @@ def algorithmic_bytes_hess(wl):
 #   tangent step: 4 stages x (locate 3 FFMA + 3 FADD, q / h 3 FMUL, per
 #     component value and gradient 11 FFMA, J q 1 FMUL + 2 FFMA, dv value
 #     7 FFMA) = 4 x 135, plus the RK4 state updates 18 FADD + 36 FFMA = 90 -> 630;
-#   adjoint step: 4 stages x (locate 3 FFMA + 3 FADD, coefficients of v . mu
-#     7 FMUL + 14 FFMA, its gradient 8 FFMA, nu 3 FMUL, scatter weights 3 FADD
-#     + 12 FMUL, corner block 24 FFMA) = 4 x 126, plus bookkeeping 12 FMUL +
-#     9 FFMA + 12 FADD = 42 -> 546.
+#   adjoint step: 4 stages x (the stage's cell and offsets read from the
+#     tangent sweep's record, no locate; coefficients of v . mu 7 FMUL +
+#     14 FFMA, its gradient 8 FFMA, nu 3 FMUL, the pending block in moment
+#     form: offset products 4 FMUL, 3 FADD + 21 FFMA) = 4 x 103, plus
+#     bookkeeping 12 FMUL + 9 FFMA + 12 FADD = 42 -> 454.
 # The coefficients themselves (13 FADD per component when a stage enters a
-# new cell) depend on the data and are not counted; ncu's executed counts are
-# in the committed profile.
-HESS_FLOPS_PER_VOXEL_STEP = 1176
+# new cell) and the block's conversion from moments to corners (12 FADD per
+# component when the cell changes) depend on the data and are not counted;
+# ncu's executed counts are in the committed profile.
+HESS_FLOPS_PER_VOXEL_STEP = 1084
 
 
 def algorithmic_flops_hess(wl):
