@@ -22,8 +22,10 @@ warmstart   the learned warm-start network (an addition, not in the paper) in
             torch CPU FP64; imported on its own (needs torch).
 
 Parity status: every function is pinned by a test against closed forms,
-invariants, library routines or brute force, except the elastic regularizer
-(``objective.elastic_*``), which the paper names but does not define:
-parity unpinned (only its self-consistency is tested).
+invariants, library routines or brute force.  The elastic regularizer, which
+the paper names but does not define, is a reading of the Navier-Lame energy;
+it is pinned by closed-form energies of fields that are linear in the cell
+centres and by its reduction to mu times the diffusion regularizer when
+lam + mu = 0.
 """
 from . import lagrangian, objective, solver  # noqa: F401

@@ -16,7 +16,8 @@ Readings of the paper taken here:
   printed ``h^3 I_n`` is read as ``h^d I_M``).
 * Elastic regularizer (Navier-Lame, mu |grad v|^2 + (lam + mu) (div v)^2, div by
   centred differences with mirrored ends): the paper names elastic models
-  but never defines one; parity unpinned.
+  but never defines one; pinned by closed forms on linear fields and by the
+  lam = -mu reduction to mu times diffusion.
 """
 from __future__ import annotations
 
