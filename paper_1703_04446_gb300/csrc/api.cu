@@ -401,8 +401,10 @@ lgnk_status forward_packed(lgnk_ctx* ctx, const float* T, float* u1, float* y) {
 }
 
 // J, D, S at the packed velocity; v is the same velocity in ABI layout (for S).
-lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, const float* R, float* grad,
-                             double* J, double* D, double* S) {
+// objective_packed in two halves: the device work with the copy of its sums
+// to hres[0..1] (no wait), and, once the stream has been synchronized, the
+// objective from them.
+lgnk_status objective_enqueue(lgnk_ctx* ctx, const float* v, const float* T, const float* R, float* grad) {
     TraceArgs a = base_args(ctx);
     a.R = R;
     a.partial = ctx->partial;
@@ -441,7 +443,11 @@ lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, cons
     // S = 1/2 dt h_v^d v^T A_reg v
     TRY(reg_apply(ctx, v, ctx->pc0, 1.0, 0.0, nullptr));
     TRY(dot_dev(ctx, v, ctx->pc0, ctx->n, 1));
-    TRY(fetch(ctx, 2));
+    CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return LGNK_OK;
+}
+
+lgnk_status objective_collect(lgnk_ctx* ctx, double* J, double* D, double* S) {
     const double Dv = 0.5 * ctx->cellvol * ctx->hres[0];
     const double Sv = 0.5 * ctx->wreg * ctx->hres[1];
     if (!std::isfinite(Dv) || !std::isfinite(Sv)) {
@@ -452,6 +458,14 @@ lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, cons
     if (S) *S = Sv;
     if (J) *J = Dv + ctx->prob.alpha * Sv;
     return LGNK_OK;
+}
+
+// J, D, S (and with grad the gradient, Eq. 9) at the packed velocity.
+lgnk_status objective_packed(lgnk_ctx* ctx, const float* v, const float* T, const float* R, float* grad,
+                             double* J, double* D, double* S) {
+    TRY(objective_enqueue(ctx, v, T, R, grad));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return objective_collect(ctx, J, D, S);
 }
 
 // out = J^T h^d J dv + alpha dt h_v^d A dv + gamma dv at the packed velocity.
@@ -516,8 +530,8 @@ lgnk_status ell(lgnk_ctx* ctx, int mode, const EllArgs& e) {
 // rows (one ELL launch instead of a second trace), with J, D, S as in
 // objective_packed.  Returns LGNK_ERR_CAPACITY when a row overflows (grad and
 // the rows are then not valid).
-lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float* R = nullptr, float* grad = nullptr,
-                            double* J = nullptr, double* D = nullptr, double* S = nullptr) {
+lgnk_status assemble_enqueue(lgnk_ctx* ctx, const float* v = nullptr, const float* R = nullptr,
+                             float* grad = nullptr) {
     ctx->asm_valid = false;
     const int W = asm_capacity(ctx->d);
     const size_t B = ((size_t)1 << ctx->d) * ctx->d;
@@ -559,7 +573,14 @@ lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float
     CK(cudaMemcpyAsync(ctx->hres + 7, ctx->dres + 7, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->hres + 6, ctx->eflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     if (nfetch) CK(cudaMemcpyAsync(ctx->hres, ctx->dres, nfetch * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    return LGNK_OK;
+}
+
+// The second half of assemble_packed, after the stream has been synchronized:
+// the row capacity check and, with_objective, J, D, S.
+lgnk_status assemble_collect(lgnk_ctx* ctx, bool with_objective, double* J = nullptr, double* D = nullptr,
+                             double* S = nullptr) {
+    const int W = asm_capacity(ctx->d);
     int flag = 0;
     memcpy(&flag, ctx->hres + 6, sizeof(int));
     ctx->asm_entries = (size_t)ctx->hres[7];
@@ -568,7 +589,7 @@ lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float
         return LGNK_ERR_CAPACITY;
     }
     ctx->asm_valid = true;
-    if (R != nullptr) {
+    if (with_objective) {
         const double Dv = 0.5 * ctx->cellvol * ctx->hres[0];
         const double Sv = 0.5 * ctx->wreg * ctx->hres[1];
         if (!std::isfinite(Dv) || !std::isfinite(Sv)) {
@@ -580,6 +601,13 @@ lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float
         if (J) *J = Dv + ctx->prob.alpha * Sv;
     }
     return LGNK_OK;
+}
+
+lgnk_status assemble_packed(lgnk_ctx* ctx, const float* v = nullptr, const float* R = nullptr, float* grad = nullptr,
+                            double* J = nullptr, double* D = nullptr, double* S = nullptr) {
+    TRY(assemble_enqueue(ctx, v, R, grad));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return assemble_collect(ctx, R != nullptr, J, D, S);
 }
 
 lgnk_status hessvec_assembled_accumulate(lgnk_ctx* ctx, const float* dv) {
@@ -793,7 +821,7 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
     ctx->npartial = std::max(ctx->trace_blocks, 2 * reduce_block_cap());
     if ((s = dalloc(ctx, (size_t)ctx->npartial, &ctx->partial)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, (size_t)ctx->trace_blocks, &ctx->cpartial)) != LGNK_OK) return fail(s);
-    if ((s = dalloc(ctx, 8, &ctx->dres)) != LGNK_OK) return fail(s);
+    if ((s = dalloc(ctx, 16, &ctx->dres)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 4, &ctx->fsc)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 1, &ctx->dcounter)) != LGNK_OK) return fail(s);
     if ((s = dalloc(ctx, 4, &ctx->dctl)) != LGNK_OK) return fail(s);
@@ -806,7 +834,7 @@ lgnk_status lgnk_create(const lgnk_problem* prob, void* stream, size_t mem_budge
         cudaGetLastError();
         return fail(LGNK_ERR_CUDA);
     }
-    if (cudaMallocHost((void**)&ctx->hres, 8 * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&ctx->hres, 16 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         ctx->hres = nullptr;
         return fail(LGNK_ERR_OOM);
@@ -1149,6 +1177,7 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             gr.key = key;
         }
         int pit = 0;
+        bool pcg_pending = false;
         if (use_graphs && lg.exec == nullptr && !lg.failed) {
             // build the loop graph; any failure falls back to one graph per iteration
             const long long l0 = ctx->launches, t0 = ctx->trace_launches;
@@ -1198,18 +1227,10 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             CK(cudaMemcpyAsync(ctx->dctl, hc, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
             CK(cudaMemcpyAsync(ctx->dres + 6, htol, sizeof(double), cudaMemcpyHostToDevice, s));
             CK(cudaGraphLaunch(lg.exec, s));
+            KL(launch_pcg_curvature_fix(x, z, ctx->dctl, n, s));
+            ctx->launches++;
             CK(cudaMemcpyAsync(hc, ctx->dctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            const int its = hc[0];
-            rep.hessvecs += its;
-            ctx->launches += its * lg.launches;
-            ctx->trace_launches += its * lg.trace_launches;
-            if (hc[2] == 2) {
-                SETERR("non-finite inner product in PCG");
-                return LGNK_ERR_NUMERIC;
-            }
-            pit = hc[1];
-            if (hc[2] == 1 && pit == 0) CK(cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            pcg_pending = true;     // the loop's counters are read at the line search's wait
         }
         for (int i = 1; lg.exec == nullptr && i <= o.max_pcg; ++i) {
             if (use_graphs && gr.exec == nullptr && !gr.failed) {
@@ -1256,34 +1277,87 @@ lgnk_status solve_impl(lgnk_ctx* ctx, const float* T, const float* R, float* v, 
             pit = i;
             if (std::sqrt(rr) <= o.pcg_rtol * gn) break;
         }
+        // Armijo backtracking on v + mu x (FP64 comparisons).  The full step
+        // mu = 1 is evaluated first together with what an accepted step needs
+        // next: its gradient (and, with the assembled J, the rows at v + x),
+        // whose objective is the trial's, bit for bit (the same trace and
+        // sums).  The slope g.x, the new |g|^2 and the PCG loop's counters
+        // come back with it in one wait.  Shorter steps, when the full one is
+        // rejected, are forward traces as before, and the gradient is then
+        // evaluated at the accepted point.
+        TRY(dot_dev(ctx, g, x, n, 8));
+        KL(launch_add_scaled(vt, v, 1.0f, x, 1.0f, n, s));
+        TRY(pack_v(ctx, vt, ctx->Vp));
+        bool spec_asm = false;
+        if (!asm_off) {
+            const lgnk_status es = assemble_enqueue(ctx, vt, R, g);
+            if (es == LGNK_OK) spec_asm = true;
+            else if (es != LGNK_ERR_OOM) return es;
+            else asm_off = true;
+        }
+        if (!spec_asm) TRY(objective_enqueue(ctx, vt, T, R, g));
+        TRY(dot_dev(ctx, g, g, n, 9));
+        CK(cudaMemcpyAsync(ctx->hres + 8, ctx->dres + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (pcg_pending) {
+            int* hc = reinterpret_cast<int*>(ctx->hpin);
+            const int its = hc[0];
+            rep.hessvecs += its;
+            ctx->launches += its * lg.launches;
+            ctx->trace_launches += its * lg.trace_launches;
+            if (hc[2] == 2) {
+                SETERR("non-finite inner product in PCG");
+                return LGNK_ERR_NUMERIC;
+            }
+            pit = hc[1];
+        }
         rep.pcg_iters += pit;
-        // Armijo backtracking on v + mu x (FP64 comparisons)
-        double slope;
-        TRY(dot_host(ctx, g, x, n, &slope));
-        double mu = 1.0, Jt = J;
-        bool accepted = false;
-        for (int ls = 0; ls < o.max_ls; ++ls) {
+        const double slope = ctx->hres[8];
+        double Jt = J, Dt = D, St = S, ggt = ctx->hres[9];
+        bool spec_rows = spec_asm;
+        if (spec_asm) {
+            const lgnk_status cs = assemble_collect(ctx, true, &Jt, &Dt, &St);
+            if (cs != LGNK_OK) {
+                if (cs != LGNK_ERR_CAPACITY && cs != LGNK_ERR_OOM) return cs;
+                // rows that do not fit: the matrix-free gradient at v + x
+                spec_rows = false;
+                TRY(objective_packed(ctx, vt, T, R, g, &Jt, &Dt, &St));
+                TRY(dot_host(ctx, g, g, n, &ggt));
+            }
+        } else {
+            TRY(objective_collect(ctx, &Jt, &Dt, &St));
+        }
+        rep.objective_evals++;
+        double mu = 1.0;
+        bool accepted = Jt <= J + o.armijo_c * mu * slope;
+        for (int ls = 1; !accepted && ls < o.max_ls; ++ls) {
+            mu *= 0.5;
             KL(launch_add_scaled(vt, v, 1.0f, x, (float)mu, n, s));
             TRY(pack_v(ctx, vt, ctx->Vp));
             TRY(objective_packed(ctx, vt, T, R, nullptr, &Jt, nullptr, nullptr));
             rep.objective_evals++;
-            if (Jt <= J + o.armijo_c * mu * slope) {
-                accepted = true;
-                break;
-            }
-            mu *= 0.5;
+            accepted = Jt <= J + o.armijo_c * mu * slope;
         }
         rep.gn_iters = it + 1;
         if (!accepted) {
             TRY(pack_v(ctx, v, ctx->Vp));
+            ctx->asm_valid = false;     // rows (if any) of the rejected full step
             status = LGNK_LS_FAILED;
             break;
         }
         CK(cudaMemcpyAsync(v, vt, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
         rep.last_mu = mu;
-        TRY(obj_grad(v));
-        rep.objective_evals++;
-        TRY(dot_host(ctx, g, g, n, &gg));
+        if (mu == 1.0) {
+            J = Jt;
+            D = Dt;
+            S = St;
+            use_asm = spec_rows;
+            gg = ggt;
+        } else {
+            TRY(obj_grad(v));
+            rep.objective_evals++;
+            TRY(dot_host(ctx, g, g, n, &gg));
+        }
         gn = std::sqrt(gg);
         if (o.verbosity > 0)
             fprintf(stderr, "lgnk GN %3d  J %.6e  D %.6e  S %.6e  |g|/|g0| %.3e  pcg %d  mu %.3g\n", it + 1, J, D,

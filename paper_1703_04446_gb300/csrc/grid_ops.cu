@@ -366,6 +366,16 @@ __global__ void pcg_control_kernel(const double* sc, int* ctl, cudaGraphConditio
     cudaGraphSetConditional(handle, go);
 }
 
+// After the device-side PCG loop: when its first iteration met non-positive
+// curvature (ctl[2] = 1 with no accepted iteration), the step is the
+// preconditioned steepest-descent direction, x = z.
+__global__ void pcg_curvature_fix_kernel(float* x, const float* __restrict__ z, const int* __restrict__ ctl,
+                                         size_t count) {
+    if (!(ctl[2] == 1 && ctl[1] == 0)) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = z[i];
+}
+
 // y = a x + b y, a = *ap when ap is given, b = *bp when bp is given.
 __global__ void axpby_dev_kernel(float a, const float* __restrict__ ap, const float* __restrict__ x, float b,
                                  const float* __restrict__ bp, float* y, size_t count) {
@@ -1198,6 +1208,14 @@ cudaError_t launch_hess_finish(int d, const void* Gp, const float* p, float* Hp,
 cudaError_t launch_pcg_update_xr(float* x, const float* p, float* r, const float* Hp, const float* f, size_t count,
                                  cudaStream_t s) {
     pcg_update_xr_kernel<<<grid_for(count), kBlock, 0, s>>>(x, p, r, Hp, f, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_curvature_fix(float* x, const float* z, const int* ctl, size_t count, cudaStream_t s) {
+    const size_t want = (count + kBlock - 1) / kBlock;
+    const int cap = reduce_block_cap();
+    const int blocks = (int)(want < (size_t)cap ? (want > 0 ? want : 1) : (size_t)cap);
+    pcg_curvature_fix_kernel<<<blocks, kBlock, 0, s>>>(x, z, ctl, count);
     return cudaGetLastError();
 }
 

@@ -137,6 +137,8 @@ cudaError_t launch_pcg_update_xr(float* x, const float* p, float* r, const float
                                  cudaStream_t s);
 // PCG loop test at the end of an iteration of a device-side while loop (see grid_ops.cu)
 cudaError_t launch_pcg_control(const double* sc, int* ctl, cudaGraphConditionalHandle handle, cudaStream_t s);
+// x = z when the device-side PCG loop's first iteration met non-positive curvature (ctl as above)
+cudaError_t launch_pcg_curvature_fix(float* x, const float* z, const int* ctl, size_t count, cudaStream_t s);
 cudaError_t launch_axpby_dev(float a, const float* ap, const float* x, float b, const float* bp, float* y,
                              size_t count, cudaStream_t s);
 // out = addsrc + scale * A x + gamma * x for the Neumann Laplacian A = B^T B of each
