@@ -494,6 +494,13 @@ lgnk_status hessvec_accumulate(lgnk_ctx* ctx, const float* T, const float* dv) {
 
 // out = the distributed slice gradients + the regularizer's term of dv.
 lgnk_status hessvec_finish(lgnk_ctx* ctx, const float* dv, float* out) {
+    if (ctx->prob.regularizer == LGNK_DIFFUSION) {
+        // the slice gradients' distribution, the Laplacian of dv and gamma dv in one pass
+        KL(launch_hess_finish(ctx->d, ctx->Gp, dv, out, ctx->vg, ctx->K, ctx->slices, 1.0f,
+                              (float)(ctx->prob.alpha * ctx->wreg), (float)ctx->prob.gamma, nullptr, 0, nullptr,
+                              nullptr, nullptr, ctx->stream));
+        return LGNK_OK;
+    }
     KL(launch_distribute_gradient(ctx->d, ctx->Gp, out, ctx->vg, ctx->K, ctx->slices, 1.0f, ctx->stream));
     return reg_apply(ctx, dv, out, ctx->prob.alpha * ctx->wreg, ctx->prob.gamma, out);
 }

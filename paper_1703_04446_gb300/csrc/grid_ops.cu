@@ -281,7 +281,7 @@ __global__ void dot_fused_kernel(const float* __restrict__ a, const float* __res
 // same order), then p.Hp into sc[2] and the step length alpha (mode 0), as
 // dot_fused_kernel does.  Launched with the same block count as the fused
 // inner products (partial holds one pair per block).
-template <int D>
+template <int D, bool DOT>
 __global__ void hess_finish_kernel(const float* __restrict__ Gp, const float* __restrict__ p, float* __restrict__ Hp,
                                    DevGrid g, int K, SliceTable tab, float gscale, float rscale, float gamma,
                                    double* partial, unsigned* counter, double* sc, float* f) {
@@ -328,10 +328,10 @@ __global__ void hess_finish_kernel(const float* __restrict__ Gp, const float* __
             if (gamma != 0.0f) r = fmaf(gamma, xi, r);
             r += gscale * acc[q];
             Hp[k] = r;
-            lsum_add_prod(dsum, xi, r);
+            if (DOT) lsum_add_prod(dsum, xi, r);
         }
     }
-    dot_blocks_finish(dsum, lsum_zero(), false, partial, counter, sc, 2, 2, 0, f);
+    if (DOT) dot_blocks_finish(dsum, lsum_zero(), false, partial, counter, sc, 2, 2, 0, f);
 }
 
 // x += f[0] p and r += f[1] Hp (the PCG updates with alpha, -alpha)
@@ -1196,12 +1196,19 @@ cudaError_t launch_dot_fused(const float* a, const float* b, const float* c, siz
 cudaError_t launch_hess_finish(int d, const void* Gp, const float* p, float* Hp, const DevGrid& g, int K,
                                const SliceTable& t, float gscale, float rscale, float gamma, double* partial,
                                int nblocks, unsigned* counter, double* sc, float* f, cudaStream_t s) {
-    if (d == 3)
-        hess_finish_kernel<3><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale, rscale, gamma,
-                                                         partial, counter, sc, f);
-    else
-        hess_finish_kernel<2><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale, rscale, gamma,
-                                                         partial, counter, sc, f);
+    // without partial: the product only, on a grid sized for the vector
+    if (partial == nullptr) nblocks = grid_for((size_t)g.m[0] * g.m[1] * g.m[2] * K);
+    if (d == 3) {
+        if (partial) hess_finish_kernel<3, true><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale,
+                                                                             rscale, gamma, partial, counter, sc, f);
+        else hess_finish_kernel<3, false><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale, rscale,
+                                                                     gamma, partial, counter, sc, f);
+    } else {
+        if (partial) hess_finish_kernel<2, true><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale,
+                                                                             rscale, gamma, partial, counter, sc, f);
+        else hess_finish_kernel<2, false><<<nblocks, kBlock, 0, s>>>((const float*)Gp, p, Hp, g, K, t, gscale, rscale,
+                                                                     gamma, partial, counter, sc, f);
+    }
     return cudaGetLastError();
 }
 
