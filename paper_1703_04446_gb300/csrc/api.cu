@@ -215,7 +215,10 @@ const char* validate_problem(const lgnk_problem* p) {
         vpad *= p->velocity.m[a] + 2 * LGNK_PAD;
         M *= p->image.m[a];
     }
-    if (ipad >= 2147483647.0 || vpad * p->time_nodes >= 2147483647.0 || M >= 2147483647.0)
+    // the packed velocity holds one slice per stage time (2N + 1) when it depends on time
+    const double slices = p->time_nodes > 1 ? 2.0 * p->rk4_steps + 1.0 : 1.0;
+    if (ipad >= 2147483647.0 || vpad * p->time_nodes >= 2147483647.0 || vpad * slices >= 2147483647.0 ||
+        M >= 2147483647.0)
         return "grid too large for 32-bit node indexing";
     return nullptr;
 }

@@ -421,7 +421,8 @@ __device__ __forceinline__ void scatter_finish(const DevGrid& g, Scatter<D>& S) 
 template <int D>
 struct BlockScatter {
     typename VecT<D>::type* G;
-    long long key;            // s0 + base of the pending cell, -1 if none
+    int key;                  // s0 + base of the pending cell, -1 if none (the packed velocity has
+                              // fewer than 2^31 elements: checked when the context is created)
     float blk[(1 << D) * D];
 };
 
@@ -449,7 +450,7 @@ __device__ __forceinline__ void scatter_finish(const DevGrid& g, BlockScatter<D>
 template <int D>
 __device__ __forceinline__ void scatter_add(const DevGrid& g, BlockScatter<D>& S, size_t s0, int base, const float* f,
                                             const float* mu) {
-    const long long key = (long long)s0 + base;
+    const int key = (int)s0 + base;
     if (key != S.key) {
         if (S.key >= 0) block_flush<D>(g, S);
         S.key = key;
@@ -585,7 +586,7 @@ __device__ __forceinline__ void stage_adjoint(const DevGrid& g, const float* __r
 template <int D, bool DV>
 struct CellCache {
     static constexpr int NC = 1 << D;
-    long long key;            // s0 + base of the cached cell, -1 when empty
+    int key;                  // s0 + base of the cached cell, -1 when empty (32 bits: see BlockScatter)
     float a[D][NC];           // coefficients of v, per component
     float b[DV ? D : 1][DV ? NC : 1];   // of dv
 };
@@ -610,7 +611,7 @@ __device__ __forceinline__ void poly_coeffs(const float* c, float* a) {
 template <int D, bool DV>
 __device__ __forceinline__ void cache_cell(const DevGrid& g, const float* __restrict__ V, const float* __restrict__ dV,
                                            size_t s0, int base, CellCache<D, DV>& C) {
-    const long long key = (long long)s0 + base;
+    const int key = (int)s0 + base;
     if (key == C.key) return;
     C.key = key;
     float cv[1 << D][D], cd[DV ? (1 << D) : 1][D];
