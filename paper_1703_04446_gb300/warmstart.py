@@ -11,7 +11,7 @@ Pipeline, on one GPU, through the lgnk C ABI:
      Adam with a cosine learning-rate decay) on (T, R) -> v*;
   4. evaluation on held-out pairs: Gauss-Newton from v = 0 with |g| <= 1e-3
      |g(0)| against Gauss-Newton from the prediction to the same absolute
-     gradient norm.  The solver stays the judge: when the prediction does not
+     gradient norm.  The solver has the last word: when the prediction does not
      lower the objective below J(0), the solve starts from zero instead.
 
 ``python -m paper_1703_04446_gb300.warmstart`` runs the whole pipeline and

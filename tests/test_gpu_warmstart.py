@@ -137,7 +137,7 @@ def test_rejects_batches_over_the_maximum():
 def test_pipeline_end_to_end_small():
     """The whole learned-warm-start pipeline on a few pairs: solver-made
     targets, training, then warm-started solves that reach the zero-start
-    solves' gradient norm (the solver stays the judge of the prediction)."""
+    solves' gradient norm (the solver has the last word on the prediction)."""
     from paper_1703_04446_gb300 import warmstart as WS
     out = WS.run(n_train=16, n_test=4, channels=4, epochs=2, batch=8)
     ev = out["eval"]
