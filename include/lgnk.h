@@ -203,7 +203,8 @@ typedef struct {
     int gn_iters;
     int pcg_iters;
     int hessvecs;
-    int objective_evals;
+    int objective_evals;  /* objective evaluations: the start, one per line-search trial (the full step's  */
+                          /* trial also yields the next gradient), one per gradient at a shorter step     */
     double J0, J, D, S;
     double g0, g;
     double seconds;
@@ -218,10 +219,15 @@ void lgnk_solve_opts_default(lgnk_solve_opts* opts);
 /* Inexact Gauss-Newton-Krylov with Armijo line search (Eq. 11): from the
  * initial v_inout[n] (device, overwritten with the result), minimise J for the
  * template T[M] and reference R[M].  Hessian products, preconditioner, vector
- * updates and inner products (FP64 sums) run on the device; the host drives the loop
- * and reads one scalar per reduction.  opts may be NULL (defaults); report may
- * be NULL.  Returns LGNK_OK on convergence, LGNK_NOT_CONVERGED at the GN cap,
- * LGNK_LS_FAILED when the line search stalls. */
+ * updates and inner products (FP64 sums) run on the device; the host drives the loop.
+ * After each PCG loop the full step is evaluated together with the gradient
+ * (and, with matvec = 1, the rows of J) at v + x, and the host reads its
+ * objective, the slope g.x, the new |g| and the PCG counters in one wait; a
+ * rejected full step backtracks by halving with objective-only trials.  opts
+ * may be NULL (defaults); report may be NULL.  Returns LGNK_OK on convergence,
+ * LGNK_NOT_CONVERGED at the GN cap, LGNK_LS_FAILED when the line search stalls
+ * (v_inout then holds the last accepted iterate, and the context's assembled J,
+ * if any, is no longer valid). */
 lgnk_status lgnk_solve(lgnk_ctx* ctx, const float* T, const float* R, float* v_inout,
                        const lgnk_solve_opts* opts, lgnk_solve_report* report);
 
