@@ -127,7 +127,12 @@ def test_continuity_256_iterates_under_the_oracle():
         g = gradient(op, v64, T64, R64)
         gn = float(np.linalg.norm(g))
         assert abs(rep["J0"] - J) <= 1e-5 * J, k
-        assert abs(rep["g0"] - gn) <= 1e-5 * gn, k
+        # |g| to 5e-5: where a stage position lies within ~1e-7 cells of a cell
+        # face, FP32 and FP64 take different cells (the kink of the linear
+        # interpolant); with 65536 particles, 64 stages and the adjoint sweep a
+        # handful of such particles per gradient is expected, and one run in
+        # about ten saw 2e-5 after two GN steps (otherwise <= 2e-6)
+        assert abs(rep["g0"] - gn) <= 5e-5 * gn, k
         assert rep["last_mu"] > 0.0, k
         vn64 = v_next.cpu().numpy().astype(np.float64)
         x = (vn64 - v64) / rep["last_mu"]
