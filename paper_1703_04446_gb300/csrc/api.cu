@@ -217,7 +217,8 @@ const char* validate_problem(const lgnk_problem* p) {
     }
     // the packed velocity holds one slice per stage time (2N + 1) when it depends on time
     const double slices = p->time_nodes > 1 ? 2.0 * p->rk4_steps + 1.0 : 1.0;
-    if (ipad >= 2147483647.0 || vpad * p->time_nodes >= 2147483647.0 || vpad * slices >= 2147483647.0 ||
+    // (the grid kernels index every array, velocity blocks of K x d components included, in 32 bits)
+    if (ipad >= 2147483647.0 || vpad * p->time_nodes * d >= 2147483647.0 || vpad * slices >= 2147483647.0 ||
         M >= 2147483647.0)
         return "grid too large for 32-bit node indexing";
     return nullptr;

@@ -24,6 +24,18 @@ __device__ __forceinline__ size_t padded_size(const DevGrid& g) {
 
 // ---------------------------------------------------------------- packing --
 
+// Axis coordinates of element i of an nx x ny (x nz) block, in 32-bit
+// arithmetic: every array the library accepts has fewer than 2^31 elements
+// (checked when the context is created), and a 64-bit division costs many
+// times a 32-bit one.
+__device__ __forceinline__ void split_xyz(unsigned i, unsigned nx, unsigned ny, int& x, int& y, int& z) {
+    const unsigned r = i / nx;
+    x = (int)(i - r * nx);
+    const unsigned q = r / ny;
+    y = (int)(r - q * ny);
+    z = (int)q;
+}
+
 // Pair-packed time slices: element (m, node) holds the velocity at stage time
 // t_m (linear in time between the K nodes) at the padded node and at its +x
 // neighbour, [v(node) | v(node + 1)], as 8 floats (3D: xyz + zero pad, twice;
@@ -42,13 +54,13 @@ __global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restr
             if (D == 3) reinterpret_cast<float4*>(Gz)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             else reinterpret_cast<float2*>(Gz)[i] = make_float2(0.0f, 0.0f);
         }
-        const int m = (int)(i / nodes);
-        const size_t node = i % nodes;
+        const unsigned nn = (unsigned)nodes;
+        const int m = (int)((unsigned)i / nn);
+        const unsigned node = (unsigned)i - (unsigned)m * nn;
         const int j = tab.j[m];
         const float th = tab.th[m];
-        const int px = (int)(node % g.mp[0]);
-        const int py = (int)((node / g.mp[0]) % g.mp[1]);
-        const int pz = (int)(node / ((size_t)g.mp[0] * g.mp[1]));
+        int px, py, pz;
+        split_xyz(node, (unsigned)g.mp[0], (unsigned)g.mp[1], px, py, pz);
         float out[PS];
 #pragma unroll
         for (int q = 0; q < PS; ++q) out[q] = 0.0f;
@@ -77,9 +89,9 @@ __global__ void pack_velocity_kernel(const float* __restrict__ v, float* __restr
 // Cell coordinates of node s of an (unpadded) velocity block.
 template <int D>
 __device__ __forceinline__ void coords(size_t s, const DevGrid& g, int* c) {
-    c[0] = (int)(s % g.m[0]);
-    c[1] = (int)((s / g.m[0]) % g.m[1]);
-    c[2] = (D == 3) ? (int)(s / ((size_t)g.m[0] * g.m[1])) : 0;
+    int z;
+    split_xyz((unsigned)s, (unsigned)g.m[0], (unsigned)g.m[1], c[0], c[1], z);
+    c[2] = (D == 3) ? z : 0;
 }
 
 // Adjoint of the slice packing for the gradient: node j of component c gets
@@ -91,11 +103,10 @@ __global__ void distribute_gradient_kernel(const float* __restrict__ Gp, float* 
     const size_t nodes = padded_size(g);
     const size_t total = Mv * K;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t s = i % Mv;
-        const int j = (int)(i / Mv);
-        const int x = (int)(s % g.m[0]);
-        const int y = (int)((s / g.m[0]) % g.m[1]);
-        const int z = (int)(s / ((size_t)g.m[0] * g.m[1]));
+        const int j = (int)((unsigned)i / (unsigned)Mv);
+        const size_t s = (unsigned)i - (unsigned)j * (unsigned)Mv;
+        int x, y, z;
+        split_xyz((unsigned)s, (unsigned)g.m[0], (unsigned)g.m[1], x, y, z);
         const size_t node = ((size_t)(z + (D == 3 ? LGNK_PAD : 0)) * g.mp[1] + (y + LGNK_PAD)) * g.mp[0] + (x + LGNK_PAD);
         float acc[3] = {0.0f, 0.0f, 0.0f};
         for (int m = 0; m < tab.n; ++m) {
@@ -120,9 +131,8 @@ __global__ void distribute_gradient_kernel(const float* __restrict__ Gp, float* 
 __global__ void pack_image_kernel(const float* __restrict__ T, float* __restrict__ Tp, DevGrid g, int d, float scale) {
     const size_t total = padded_size(g);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int px = (int)(i % g.mp[0]);
-        const int py = (int)((i / g.mp[0]) % g.mp[1]);
-        const int pz = (int)(i / ((size_t)g.mp[0] * g.mp[1]));
+        int px, py, pz;
+        split_xyz((unsigned)i, (unsigned)g.mp[0], (unsigned)g.mp[1], px, py, pz);
         const int x = px - LGNK_PAD, y = py - LGNK_PAD, z = (d == 3) ? pz - LGNK_PAD : 0;
         const bool in = x >= 0 && x < g.m[0] && y >= 0 && y < g.m[1] && z >= 0 && z < g.m[2];
         Tp[i] = in ? scale * T[((size_t)z * g.m[1] + y) * g.m[0] + x] : 0.0f;
@@ -132,9 +142,8 @@ __global__ void pack_image_kernel(const float* __restrict__ T, float* __restrict
 __global__ void unpack_image_kernel(const float* __restrict__ acc, float* __restrict__ out, DevGrid g, int d) {
     const size_t M = (size_t)g.m[0] * g.m[1] * g.m[2];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.m[0]);
-        const int y = (int)((i / g.m[0]) % g.m[1]);
-        const int z = (int)(i / ((size_t)g.m[0] * g.m[1]));
+        int x, y, z;
+        split_xyz((unsigned)i, (unsigned)g.m[0], (unsigned)g.m[1], x, y, z);
         const size_t p = ((size_t)(z + (d == 3 ? LGNK_PAD : 0)) * g.mp[1] + (y + LGNK_PAD)) * g.mp[0] + (x + LGNK_PAD);
         out[i] = acc[p];
     }
@@ -143,9 +152,8 @@ __global__ void unpack_image_kernel(const float* __restrict__ acc, float* __rest
 __global__ void repad_image_kernel(float* acc, DevGrid g, int d, float scale) {
     const size_t total = padded_size(g);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int px = (int)(i % g.mp[0]);
-        const int py = (int)((i / g.mp[0]) % g.mp[1]);
-        const int pz = (int)(i / ((size_t)g.mp[0] * g.mp[1]));
+        int px, py, pz;
+        split_xyz((unsigned)i, (unsigned)g.mp[0], (unsigned)g.mp[1], px, py, pz);
         const int x = px - LGNK_PAD, y = py - LGNK_PAD, z = (d == 3) ? pz - LGNK_PAD : 0;
         const bool in = x >= 0 && x < g.m[0] && y >= 0 && y < g.m[1] && z >= 0 && z < g.m[2];
         acc[i] = in ? scale * acc[i] : 0.0f;
@@ -180,9 +188,8 @@ __global__ void residual_kernel(const float* __restrict__ u1, const float* __res
         const float r = ui - Ri;
         lsum_add_sqdiff(s, ui, Ri);
         if (rp != nullptr) {
-            const int x = (int)(i % g.m[0]);
-            const int y = (int)((i / g.m[0]) % g.m[1]);
-            const int z = (int)(i / ((size_t)g.m[0] * g.m[1]));
+            int x, y, z;
+            split_xyz((unsigned)i, (unsigned)g.m[0], (unsigned)g.m[1], x, y, z);
             const size_t p = ((size_t)(z + (d == 3 ? LGNK_PAD : 0)) * g.mp[1] + (y + LGNK_PAD)) * g.mp[0] + (x + LGNK_PAD);
             rp[p] = scale * r;
         }
@@ -291,8 +298,8 @@ __global__ void hess_finish_kernel(const float* __restrict__ Gp, const float* __
     const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
     lsum dsum = lsum_zero();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t sn = i % Mv;
-        const int j = (int)(i / Mv);
+        const int j = (int)((unsigned)i / (unsigned)Mv);
+        const size_t sn = (unsigned)i - (unsigned)j * (unsigned)Mv;
         int c[3];
         coords<D>(sn, g, c);
         const size_t node =
@@ -404,7 +411,7 @@ __global__ void laplacian_kernel(const float* __restrict__ x, float* out, DevGri
     const size_t total = Mv * nblk;
     const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t s = i % Mv;
+        const size_t s = (unsigned)i % (unsigned)Mv;
         int c[3];
         coords<D>(s, g, c);
         const float xi = x[i];
@@ -430,8 +437,8 @@ __global__ void divergence_kernel(const float* __restrict__ x, float* __restrict
     const size_t total = Mv * K;
     const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t s = i % Mv;
-        const size_t j = i / Mv;
+        const size_t s = (unsigned)i % (unsigned)Mv;
+        const size_t j = (unsigned)i / (unsigned)Mv;
         int c[3];
         coords<D>(s, g, c);
         float acc = 0.0f;
@@ -454,8 +461,8 @@ __global__ void elastic_kernel(const float* __restrict__ x, const float* __restr
     const size_t total = Mv * K * D;
     const size_t stride[3] = {1, (size_t)g.m[0], (size_t)g.m[0] * g.m[1]};
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t s = i % Mv;
-        const size_t blk = i / Mv;
+        const size_t s = (unsigned)i % (unsigned)Mv;
+        const size_t blk = (unsigned)i / (unsigned)Mv;
         const int comp = (int)(blk % D);
         const size_t j = blk / D;
         int c[3];
@@ -496,7 +503,7 @@ __global__ void dct_axis_kernel(const float* __restrict__ in, float* __restrict_
     const int m = g.m[axis];
     const size_t st = (axis == 0) ? 1 : (axis == 1 ? (size_t)g.m[0] : (size_t)g.m[0] * g.m[1]);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t s = i % Mv;
+        const size_t s = (unsigned)i % (unsigned)Mv;
         const int k = (int)((s / st) % m);
         const size_t base = i - (size_t)k * st;
         float acc = 0.0f;
